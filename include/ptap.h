@@ -1,0 +1,197 @@
+/*
+ * ptap.h -- C ABI of the GB300 all-at-once sparse triple product C = P^T A P.
+ *
+ * The operation (Kong, "Parallel memory-efficient all-at-once algorithms for
+ * the sparse matrix triple products in multigrid methods"):
+ *
+ *   A is n x n, P is n x m (Section 2), C = P^T A P is m x m (Section 3,
+ *   Eq. 4).  C is formed all at once as a sum of outer products of the rows of
+ *   P and the rows of A P (Eq. 9), so neither A P nor P^T is ever stored.  The
+ *   work splits into a symbolic phase that preallocates C without any
+ *   floating point (Section 2, Alg. 1-2; Section 3, Alg. 7) and a numeric
+ *   phase that fills the preallocated values (Alg. 8) and may be repeated
+ *   whenever the values of A or P change (Section 4.1: one symbolic and
+ *   eleven numeric products; Section 4.2, Table 8: caching symbolic data).
+ *
+ * Conventions for every entry point:
+ *  - Matrices are CSR with int32 row pointers and column indices.  Columns
+ *    must be sorted ascending and unique within each row; duplicates are
+ *    rejected, not summed.  Explicitly stored zeros are structural entries.
+ *  - Values are float64 (PTAP_F64) or float32 (PTAP_F32); A, P and C of one
+ *    plan share one dtype.  float32 plans accumulate in float32.
+ *  - Every pointer in a ptap_csr and every value buffer is a DEVICE pointer
+ *    owned by the caller, unless stated otherwise.  The library never frees
+ *    caller memory.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Calls are asynchronous on it, except where a call says it
+ *    synchronises.
+ *  - Every call returns PTAP_OK (0) or one of the PTAP_ERR_* codes below; no
+ *    C++ exception crosses this boundary.  A failed call leaves its outputs
+ *    unspecified and allocates nothing that outlives it.
+ *  - C's pattern is structural: an entry reached through the patterns of P,
+ *    A and P is kept even where its value cancels to zero.  Column indices of
+ *    C are sorted ascending per row; rows may be empty.
+ */
+#ifndef PTAP_H
+#define PTAP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- error codes ------------------------------------------------------ */
+#define PTAP_OK 0
+#define PTAP_ERR_INVALID 1     /* null pointer, shape or dtype mismatch, bad CSR */
+#define PTAP_ERR_PATTERN 2     /* inputs do not match the pattern the plan was built for */
+#define PTAP_ERR_OVERFLOW 3    /* nnz(C) or an intermediate count >= 2^31 */
+#define PTAP_ERR_OOM 4         /* an allocation failed */
+#define PTAP_ERR_SPILL 5       /* a device hash table ran out of space (status word) */
+#define PTAP_ERR_TIMEOUT 6     /* a bounded device wait gave up */
+#define PTAP_ERR_CUDA 7        /* any other CUDA failure */
+#define PTAP_ERR_UNSUPPORTED 8 /* a valid request this build does not implement */
+
+/* ---- types ------------------------------------------------------------ */
+typedef enum { PTAP_F64 = 0, PTAP_F32 = 1 } ptap_dtype;
+
+/* A CSR matrix on the device.  row_ptr has nrows+1 entries, col_idx and val
+ * nnz entries; nnz must equal row_ptr[nrows].  val may be NULL for calls that
+ * only need the pattern.  All pointers are caller-owned device memory. */
+typedef struct {
+  int32_t nrows;
+  int32_t ncols;
+  int64_t nnz;
+  const int32_t* row_ptr;
+  const int32_t* col_idx;
+  const void* val;
+  int32_t dtype; /* ptap_dtype */
+} ptap_csr;
+
+/* Optional device allocator.  alloc returns device memory of `bytes` bytes
+ * usable on `stream` (NULL on failure); free releases it.  When a NULL
+ * allocator is passed the library uses cudaMallocAsync/cudaFreeAsync on the
+ * call's stream. */
+typedef struct {
+  void* (*alloc)(size_t bytes, void* stream, void* ctx);
+  void (*free)(void* ptr, size_t bytes, void* stream, void* ctx);
+  void* ctx;
+} ptap_allocator;
+
+/* Numeric scheme. */
+#define PTAP_MODE_AUTO 0
+#define PTAP_MODE_OWNER 1  /* coarse-row chunks accumulated on chip, written once */
+#define PTAP_MODE_ATOMIC 2 /* Alg. 8 literally: per fine row, atomic scatter into C */
+
+/* Tuning knobs; zero selects the built-in default for a field. */
+typedef struct {
+  int32_t mode;           /* PTAP_MODE_* */
+  int32_t chunk_entries;  /* C entries accumulated per CTA in owner mode */
+  int32_t block_threads;  /* threads per CTA of the numeric kernels */
+  int32_t group_lanes;    /* lanes that cooperate on one fine row: 4, 8, 16 or 32 */
+  int32_t ap_slots;       /* hash slots per group for one row of A P */
+  int32_t debug_checks;   /* nonzero: validate CSR inputs on the device */
+  int32_t force_spill;    /* nonzero: shrink on-chip tables to exercise spill paths */
+  int32_t reserved[9];
+} ptap_config;
+
+/* Statistics of a plan (host struct filled by ptap_plan_stats). */
+typedef struct {
+  int32_t n, m;
+  int64_t nnz_a, nnz_p, nnz_c;
+  int64_t plan_bytes;        /* device bytes the plan holds between calls */
+  int64_t peak_bytes;        /* high-water mark of library-held device bytes */
+  int64_t symbolic_peak_bytes;
+  int32_t n_chunks;          /* owner-mode chunks */
+  int32_t n_heavy_chunks;    /* chunks whose C rows exceed on-chip capacity */
+  int64_t chunk_fine_rows;   /* sum over chunks of the fine rows each visits */
+  int32_t n_spill_rows_symbolic; /* coarse rows whose pattern needed the global table */
+  int32_t mode;              /* numeric scheme the plan uses */
+  int32_t chunk_entries, block_threads, group_lanes, ap_slots;
+  int32_t kind;              /* 0 all-at-once plan, 1 two-step plan */
+  int32_t reserved[7];
+} ptap_stats;
+
+typedef struct ptap_plan ptap_plan;
+typedef struct ptap_batch ptap_batch;
+
+/* ---- entry points ----------------------------------------------------- */
+
+/* Symbolic all-at-once product (Section 3, Alg. 7; Alg. 1 for one row of
+ * A P).  Validates A (n x n) and P (n x m), computes the structural pattern
+ * of C = P^T A P and the numeric schedule, and returns a library-owned plan
+ * in *out.  Values of A and P are not read.  `cfg` and `alloc` may be NULL.
+ * Synchronises `stream` (once, to size C).  Errors: PTAP_ERR_INVALID,
+ * PTAP_ERR_OVERFLOW (nnz(C) >= 2^31), PTAP_ERR_OOM, PTAP_ERR_SPILL,
+ * PTAP_ERR_CUDA. */
+int ptap_symbolic(const ptap_csr* A, const ptap_csr* P, const ptap_config* cfg,
+                  const ptap_allocator* alloc, void* stream, ptap_plan** out);
+
+/* Pattern of C held by the plan: *m rows, *nnz entries, device pointers to
+ * row_ptr (m+1) and col_idx (nnz), owned by the plan and valid until
+ * ptap_plan_destroy.  Any output pointer may be NULL. */
+int ptap_plan_pattern(const ptap_plan* plan, int32_t* m, int64_t* nnz,
+                      const int32_t** row_ptr, const int32_t** col_idx);
+
+/* Numeric all-at-once product (Section 3, Eq. 9, Alg. 8): writes the nnz(C)
+ * values of C = P^T A P into C_val (caller-owned device buffer, dtype of the
+ * plan), in the order of the plan's pattern.  A and P must have the patterns
+ * the plan was built from (checked by shape and nnz: PTAP_ERR_PATTERN).  No
+ * auxiliary A P or P^T is formed.  Asynchronous; allocates nothing. */
+int ptap_numeric(ptap_plan* plan, const ptap_csr* A, const ptap_csr* P, void* C_val,
+                 void* stream);
+
+/* Backward of C = P^T A P (not in the paper).  Given G = dL/dC as nnz(C)
+ * values on the plan's pattern, writes dL/dA = (P G P^T) restricted to the
+ * pattern of A into dA (nnz(A) values) and dL/dP = (A P G^T + A^T P G)
+ * restricted to the pattern of P into dP (nnz(P) values).  Either output may
+ * be NULL to skip it.  Row by row, all at once: no product matrix is stored.
+ * Asynchronous; allocates nothing. */
+int ptap_backward(ptap_plan* plan, const ptap_csr* A, const ptap_csr* P, const void* G,
+                  void* dA, void* dP, void* stream);
+
+/* Two-step comparator (Section 3, Eq. 6, Alg. 5-6): builds C~ = A P and P^T
+ * explicitly, then C = P^T C~.  The symbolic call returns a plan of kind 1
+ * that holds those auxiliary matrices; ptap_numeric on that plan runs the
+ * two-step numeric phase.  Same conventions as ptap_symbolic. */
+int ptap_two_step_symbolic(const ptap_csr* A, const ptap_csr* P, const ptap_config* cfg,
+                           const ptap_allocator* alloc, void* stream, ptap_plan** out);
+
+/* Batched numeric products (uneven sizes, one persistent launch).  `plans`,
+ * `A` and `P` (host arrays of `count` elements) and `C_vals` (host array of
+ * device pointers) fix the problems once; the batch copies their descriptors
+ * to the device.  All plans must be all-at-once plans of one dtype. */
+int ptap_batch_create(ptap_plan* const* plans, const ptap_csr* A, const ptap_csr* P,
+                      void* const* C_vals, int32_t count, const ptap_allocator* alloc,
+                      void* stream, ptap_batch** out);
+
+/* Runs every product of the batch in one launch over a binned work queue.
+ * Reads the current values behind the pointers given at creation, so it can
+ * be captured once in a CUDA graph and replayed after the values change.
+ * Asynchronous; allocates nothing. */
+int ptap_batch_numeric(ptap_batch* batch, void* stream);
+
+void ptap_batch_destroy(ptap_batch* batch);
+
+/* Statistics of a plan; see ptap_stats. */
+int ptap_plan_stats(const ptap_plan* plan, ptap_stats* out);
+
+/* Reads and clears the plan's device status word (synchronises `stream`):
+ * PTAP_OK, or the PTAP_ERR_* code a kernel of this plan recorded. */
+int ptap_plan_check(ptap_plan* plan, void* stream);
+
+/* Frees everything the plan holds (stream-ordered on the plan's stream). */
+void ptap_plan_destroy(ptap_plan* plan);
+
+/* Static description of an error code. */
+const char* ptap_error_string(int code);
+
+/* Version of this library as major*10000 + minor*100 + patch. */
+int ptap_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PTAP_H */

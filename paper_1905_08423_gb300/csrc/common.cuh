@@ -1,0 +1,266 @@
+// Internal declarations shared by the translation units of libptap.
+// Not part of the public ABI (that is include/ptap.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdio>
+#include <cstring>
+#include <unordered_map>
+#include <vector>
+
+#include "ptap.h"
+
+namespace ptap {
+
+// ---------------------------------------------------------------------------
+// error handling: no exception crosses the ABI; internal code returns codes.
+// ---------------------------------------------------------------------------
+#define PTAP_TRY(expr)            \
+  do {                            \
+    int _rc = (expr);             \
+    if (_rc != PTAP_OK) return _rc; \
+  } while (0)
+
+#define PTAP_CUDA(expr)                                   \
+  do {                                                    \
+    cudaError_t _e = (expr);                              \
+    if (_e != cudaSuccess) {                              \
+      ptap::note_cuda_error(_e, #expr, __FILE__, __LINE__); \
+      return PTAP_ERR_CUDA;                               \
+    }                                                     \
+  } while (0)
+
+void note_cuda_error(cudaError_t e, const char* what, const char* file, int line);
+
+// Launch check: a bad launch configuration is a CUDA error of this call.
+#define PTAP_LAUNCHED() PTAP_CUDA(cudaGetLastError())
+
+// ---------------------------------------------------------------------------
+// device memory: every library allocation goes through one tracker so that a
+// plan can report its live and peak bytes (the memory the paper compares).
+// ---------------------------------------------------------------------------
+struct Tracker {
+  ptap_allocator user{};
+  bool has_user = false;
+  cudaStream_t stream = nullptr;
+  int64_t live = 0, peak = 0;
+  std::unordered_map<void*, size_t> sizes;
+
+  void init(const ptap_allocator* a, cudaStream_t s) {
+    stream = s;
+    if (a && a->alloc && a->free) {
+      user = *a;
+      has_user = true;
+    }
+  }
+  // Returns PTAP_OK and *p, or PTAP_ERR_OOM.  Zero-byte requests give a
+  // small real allocation so that pointers are never NULL.
+  int get(void** p, size_t bytes) {
+    size_t b = bytes ? bytes : 16;
+    b = (b + 255) & ~size_t(255);
+    void* q = nullptr;
+    if (has_user) {
+      q = user.alloc(b, (void*)stream, user.ctx);
+    } else if (cudaMallocAsync(&q, b, stream) != cudaSuccess) {
+      cudaGetLastError();
+      q = nullptr;
+    }
+    if (!q) return PTAP_ERR_OOM;
+    sizes[q] = b;
+    live += (int64_t)b;
+    if (live > peak) peak = live;
+    *p = q;
+    return PTAP_OK;
+  }
+  template <typename T>
+  int get_n(T** p, int64_t n) {
+    return get((void**)p, (size_t)(n < 0 ? 0 : n) * sizeof(T));
+  }
+  void put(void* p) {
+    if (!p) return;
+    auto it = sizes.find(p);
+    size_t b = it == sizes.end() ? 0 : it->second;
+    if (it != sizes.end()) sizes.erase(it);
+    live -= (int64_t)b;
+    if (has_user) user.free(p, b, (void*)stream, user.ctx);
+    else cudaFreeAsync(p, stream);
+  }
+  void release_all() {
+    for (auto& kv : sizes) {
+      if (has_user) user.free(kv.first, kv.second, (void*)stream, user.ctx);
+      else cudaFreeAsync(kv.first, stream);
+    }
+    sizes.clear();
+    live = 0;
+  }
+};
+
+// RAII scratch for the duration of one call.
+struct Scratch {
+  Tracker* t;
+  std::vector<void*> bufs;
+  explicit Scratch(Tracker* tr) : t(tr) {}
+  template <typename T>
+  int get(T** p, int64_t n) {
+    int rc = t->get_n(p, n);
+    if (rc == PTAP_OK) bufs.push_back((void*)*p);
+    return rc;
+  }
+  void release(void* p) {
+    for (auto& b : bufs)
+      if (b == p) {
+        t->put(p);
+        b = nullptr;
+      }
+  }
+  ~Scratch() {
+    for (void* b : bufs)
+      if (b) t->put(b);
+  }
+};
+
+// ---------------------------------------------------------------------------
+// resolved configuration
+// ---------------------------------------------------------------------------
+struct Config {
+  int mode = PTAP_MODE_OWNER;
+  int chunk_entries = 4096;
+  int block_threads = 256;
+  int group_lanes = 8;
+  int ap_slots = 64;
+  int debug_checks = 0;
+  int force_spill = 0;
+};
+
+Config resolve_config(const ptap_config* c);
+
+// ---------------------------------------------------------------------------
+// device-side CSR views
+// ---------------------------------------------------------------------------
+struct CsrI {  // pattern only
+  int32_t nrows, ncols;
+  const int32_t* rp;
+  const int32_t* ci;
+};
+template <typename V>
+struct CsrV {
+  int32_t nrows, ncols;
+  const int32_t* rp;
+  const int32_t* ci;
+  const V* val;
+};
+
+// ---------------------------------------------------------------------------
+// the plan
+// ---------------------------------------------------------------------------
+struct TwoStepData;
+
+}  // namespace ptap
+
+struct ptap_plan {
+  int kind = 0;  // 0 all-at-once, 1 two-step
+  int dtype = PTAP_F64;
+  int32_t n = 0, m = 0;
+  int64_t nnz_a = 0, nnz_p = 0, nnz_c = 0;
+  ptap::Tracker mem;
+  cudaStream_t stream = nullptr;
+  ptap::Config cfg;
+  int64_t symbolic_peak = 0;
+  int32_t spill_rows = 0;
+
+  int32_t* c_rp = nullptr;  // C pattern (plan-owned)
+  int32_t* c_ci = nullptr;
+
+  // owner-mode numeric schedule
+  int32_t nchunks = 0, nheavy = 0, max_chunk_rows = 0, max_chunk_nnz = 0;
+  int32_t* chunk_row = nullptr;   // [nchunks+1] first coarse row of each chunk
+  int32_t* chunk_fptr = nullptr;  // [nchunks+1] offsets into chunk_frows
+  int32_t* chunk_frows = nullptr; // fine rows visited per chunk, ascending
+  int64_t nfrows = 0;
+
+  int32_t* status = nullptr;  // device status word (PTAP_* code, 0 = ok)
+
+  // launch configuration of the numeric kernel, settled at symbolic time
+  size_t num_smem = 0;
+  int num_per_sm = 0;
+
+  ptap::TwoStepData* two = nullptr;
+};
+
+struct ptap_batch {
+  ptap::Tracker mem;
+  int dtype = PTAP_F64;
+  int32_t count = 0;
+  int64_t total_items = 0;
+  void* d_desc = nullptr;     // device array of per-problem descriptors
+  int32_t* d_items = nullptr; // work items: (problem, chunk) pairs, heavy first
+  int32_t* d_counter = nullptr;
+  int32_t* status = nullptr;
+  int32_t max_chunk_nnz = 0, max_chunk_rows = 0;
+  ptap::Config cfg;
+  size_t smem = 0;  // launch configuration, settled at creation
+  int grid = 0;
+};
+
+namespace ptap {
+
+// ---------------------------------------------------------------------------
+// shared host helpers (implemented in the .cu files named)
+// ---------------------------------------------------------------------------
+// scan.cu: exclusive scan of n int32 counts into out[0..n] (out[n] = total);
+// PTAP_ERR_OVERFLOW if the total reaches 2^31.  *total receives the total
+// (synchronises the stream when total != nullptr).
+int exclusive_scan(Tracker& mem, const int32_t* in, int32_t* out, int64_t n,
+                   int64_t* total, cudaStream_t s);
+// scan.cu: sorts each segment [ptr[r], ptr[r+1]) of keys ascending (and the
+// optional companion values alongside).
+int segmented_sort(Tracker& mem, const int32_t* ptr, int32_t nseg, int32_t* keys,
+                   int32_t* vals, int32_t max_len, cudaStream_t s);
+// symbolic.cu: transpose of a CSR pattern: tp (ncols+1), tj (nnz) fine-row
+// ids per column sorted ascending, and tperm (nnz, optional) = position in
+// the source of each transposed entry.
+int transpose_pattern(Tracker& mem, const CsrI& M, int32_t* tp, int32_t* tj,
+                      int32_t* tperm, cudaStream_t s);
+// validation of a CSR input (device); returns PTAP_ERR_INVALID on a bad matrix.
+int validate_csr(Tracker& mem, const ptap_csr* M, cudaStream_t s);
+int check_csr_host(const ptap_csr* M, bool need_val);
+
+// numeric.cu
+int prepare_numeric(ptap_plan* p);
+int numeric_owner(ptap_plan* p, const ptap_csr* A, const ptap_csr* P, void* C, cudaStream_t s);
+int numeric_atomic(ptap_plan* p, const ptap_csr* A, const ptap_csr* P, void* C, cudaStream_t s);
+// twostep.cu
+int two_step_numeric(ptap_plan* p, const ptap_csr* A, const ptap_csr* P, void* C, cudaStream_t s);
+void two_step_free(ptap_plan* p);
+
+// ---------------------------------------------------------------------------
+// device helpers
+// ---------------------------------------------------------------------------
+// Empty hash slot.  Column indices are < ncols <= INT32_MAX, so never equal;
+// empty slots also sort after every key.
+constexpr int32_t kEmpty = 0x7fffffff;
+
+__host__ __device__ inline uint32_t hash32(uint32_t k) { return k * 0x9E3779B1u; }
+
+__host__ __device__ inline int ilog2_ceil(uint32_t x) {
+  int r = 0;
+  while ((1u << r) < x) ++r;
+  return r;
+}
+
+inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+inline int num_sms() {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+  }
+  return sms;
+}
+
+}  // namespace ptap

@@ -1,0 +1,369 @@
+"""Python binding of the C ABI in include/ptap.h (argument marshalling only).
+
+Every step of the triple product runs in the CUDA library ``libptap.so``;
+this module passes device pointers and sizes across the ABI with ctypes.
+PyTorch supplies device memory (its caching allocator is handed to the library
+as a ``ptap_allocator``) and streams.  There is no CPU fallback: if the
+library cannot be loaded, every call raises.
+
+Names follow the ABI: ``symbolic`` / ``numeric`` / ``backward`` /
+``two_step_symbolic`` / ``Batch``; ``PtAP`` is the autograd Function.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import torch
+
+from . import build as _build
+
+_c = ctypes
+F64, F32 = 0, 1
+MODE_AUTO, MODE_OWNER, MODE_ATOMIC = 0, 1, 2
+
+ERRORS = {1: "PTAP_ERR_INVALID", 2: "PTAP_ERR_PATTERN", 3: "PTAP_ERR_OVERFLOW",
+          4: "PTAP_ERR_OOM", 5: "PTAP_ERR_SPILL", 6: "PTAP_ERR_TIMEOUT",
+          7: "PTAP_ERR_CUDA", 8: "PTAP_ERR_UNSUPPORTED"}
+
+
+class PtapError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        msg = _lib().ptap_error_string(code).decode() if _LIB is not None else ""
+        super().__init__(f"{where}: {ERRORS.get(code, code)} ({msg})")
+
+
+class _Csr(_c.Structure):
+    _fields_ = [("nrows", _c.c_int32), ("ncols", _c.c_int32), ("nnz", _c.c_int64),
+                ("row_ptr", _c.c_void_p), ("col_idx", _c.c_void_p), ("val", _c.c_void_p),
+                ("dtype", _c.c_int32)]
+
+
+_ALLOC_FN = _c.CFUNCTYPE(_c.c_void_p, _c.c_size_t, _c.c_void_p, _c.c_void_p)
+_FREE_FN = _c.CFUNCTYPE(None, _c.c_void_p, _c.c_size_t, _c.c_void_p, _c.c_void_p)
+
+
+class _Allocator(_c.Structure):
+    _fields_ = [("alloc", _ALLOC_FN), ("free", _FREE_FN), ("ctx", _c.c_void_p)]
+
+
+class _Config(_c.Structure):
+    _fields_ = [("mode", _c.c_int32), ("chunk_entries", _c.c_int32),
+                ("block_threads", _c.c_int32), ("group_lanes", _c.c_int32),
+                ("ap_slots", _c.c_int32), ("debug_checks", _c.c_int32),
+                ("force_spill", _c.c_int32), ("reserved", _c.c_int32 * 9)]
+
+
+class _Stats(_c.Structure):
+    _fields_ = [("n", _c.c_int32), ("m", _c.c_int32), ("nnz_a", _c.c_int64),
+                ("nnz_p", _c.c_int64), ("nnz_c", _c.c_int64), ("plan_bytes", _c.c_int64),
+                ("peak_bytes", _c.c_int64), ("symbolic_peak_bytes", _c.c_int64),
+                ("n_chunks", _c.c_int32), ("n_heavy_chunks", _c.c_int32),
+                ("chunk_fine_rows", _c.c_int64), ("n_spill_rows_symbolic", _c.c_int32),
+                ("mode", _c.c_int32), ("chunk_entries", _c.c_int32),
+                ("block_threads", _c.c_int32), ("group_lanes", _c.c_int32),
+                ("ap_slots", _c.c_int32), ("kind", _c.c_int32), ("reserved", _c.c_int32 * 7)]
+
+
+_LIB = None
+_VP = _c.c_void_p
+_PP = _c.POINTER(_c.c_void_p)
+
+SYMBOLS = ["ptap_symbolic", "ptap_plan_pattern", "ptap_numeric", "ptap_backward",
+           "ptap_two_step_symbolic", "ptap_batch_create", "ptap_batch_numeric",
+           "ptap_batch_destroy", "ptap_plan_stats", "ptap_plan_check", "ptap_plan_destroy",
+           "ptap_error_string", "ptap_version"]
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def _lib():
+    """Load libptap.so (building it first if missing); raises if it cannot."""
+    global _LIB
+    if _LIB is None:
+        path = _build.LIB
+        if not os.path.exists(path) or os.environ.get("PTAP_REBUILD"):
+            path = _build.build()
+        L = _c.CDLL(path)
+        L.ptap_symbolic.argtypes = [_c.POINTER(_Csr), _c.POINTER(_Csr), _c.POINTER(_Config),
+                                    _c.POINTER(_Allocator), _VP, _PP]
+        L.ptap_two_step_symbolic.argtypes = L.ptap_symbolic.argtypes
+        L.ptap_plan_pattern.argtypes = [_VP, _c.POINTER(_c.c_int32), _c.POINTER(_c.c_int64),
+                                        _PP, _PP]
+        L.ptap_numeric.argtypes = [_VP, _c.POINTER(_Csr), _c.POINTER(_Csr), _VP, _VP]
+        L.ptap_backward.argtypes = [_VP, _c.POINTER(_Csr), _c.POINTER(_Csr), _VP, _VP, _VP, _VP]
+        L.ptap_batch_create.argtypes = [_c.POINTER(_VP), _c.POINTER(_Csr), _c.POINTER(_Csr),
+                                        _c.POINTER(_VP), _c.c_int32, _c.POINTER(_Allocator),
+                                        _VP, _PP]
+        L.ptap_batch_numeric.argtypes = [_VP, _VP]
+        L.ptap_batch_destroy.argtypes = [_VP]
+        L.ptap_batch_destroy.restype = None
+        L.ptap_plan_stats.argtypes = [_VP, _c.POINTER(_Stats)]
+        L.ptap_plan_check.argtypes = [_VP, _VP]
+        L.ptap_plan_destroy.argtypes = [_VP]
+        L.ptap_plan_destroy.restype = None
+        L.ptap_error_string.argtypes = [_c.c_int]
+        L.ptap_error_string.restype = _c.c_char_p
+        L.ptap_version.argtypes = []
+        missing = [name for name in SYMBOLS if not hasattr(L, name)]
+        if missing:
+            raise RuntimeError(f"{path} lacks {missing}")
+        _LIB = L
+    return _LIB
+
+
+def _check(rc: int, where: str):
+    if rc != 0:
+        raise PtapError(rc, where)
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+# ---------------------------------------------------------------------------
+# torch caching allocator handed to the library
+# ---------------------------------------------------------------------------
+def _py_alloc(nbytes, stream, ctx):
+    try:
+        return torch.cuda.caching_allocator_alloc(int(nbytes), torch.cuda.current_device(),
+                                                  int(stream or 0))
+    except Exception:  # out of memory: the library reports PTAP_ERR_OOM
+        return None
+
+
+def _py_free(ptr, nbytes, stream, ctx):
+    torch.cuda.caching_allocator_delete(int(ptr))
+
+
+_ALLOC_CB = _ALLOC_FN(_py_alloc)
+_FREE_CB = _FREE_FN(_py_free)
+_TORCH_ALLOCATOR = _Allocator(_ALLOC_CB, _FREE_CB, None)
+
+
+# ---------------------------------------------------------------------------
+# matrices
+# ---------------------------------------------------------------------------
+@dataclass
+class Csr:
+    """A device CSR matrix held in torch tensors (int32 indices, f32/f64 values)."""
+
+    nrows: int
+    ncols: int
+    row_ptr: torch.Tensor
+    col_idx: torch.Tensor
+    val: torch.Tensor | None
+
+    @property
+    def nnz(self) -> int:
+        return int(self.col_idx.numel())
+
+    @property
+    def dtype_code(self) -> int:
+        v = self.val
+        if v is None or v.dtype == torch.float64:
+            return F64
+        if v.dtype == torch.float32:
+            return F32
+        raise TypeError(f"unsupported value dtype {v.dtype}")
+
+    def c(self, dtype_code: int | None = None) -> _Csr:
+        for t in (self.row_ptr, self.col_idx):
+            assert t.is_cuda and t.dtype == torch.int32 and t.is_contiguous()
+        if self.val is not None:
+            assert self.val.is_cuda and self.val.is_contiguous() and self.val.numel() == self.nnz
+        return _Csr(self.nrows, self.ncols, self.nnz, self.row_ptr.data_ptr(),
+                    self.col_idx.data_ptr(), self.val.data_ptr() if self.val is not None else None,
+                    self.dtype_code if dtype_code is None else dtype_code)
+
+    def with_values(self, val: torch.Tensor) -> "Csr":
+        return Csr(self.nrows, self.ncols, self.row_ptr, self.col_idx, val)
+
+    @staticmethod
+    def from_host(M, device="cuda", dtype=torch.float64) -> "Csr":
+        """From any host CSR with nrows/ncols/row_ptr/col_idx/val (numpy)."""
+        rp = torch.as_tensor(M.row_ptr, dtype=torch.int32).to(device)
+        ci = torch.as_tensor(M.col_idx, dtype=torch.int32).to(device)
+        v = torch.as_tensor(M.val).to(device=device, dtype=dtype)
+        return Csr(M.nrows, M.ncols, rp.contiguous(), ci.contiguous(), v.contiguous())
+
+
+def make_config(mode=MODE_OWNER, chunk_entries=0, block_threads=0, group_lanes=0, ap_slots=0,
+                debug_checks=False, force_spill=False) -> _Config:
+    cfg = _Config()
+    cfg.mode = mode
+    cfg.chunk_entries = chunk_entries
+    cfg.block_threads = block_threads
+    cfg.group_lanes = group_lanes
+    cfg.ap_slots = ap_slots
+    cfg.debug_checks = int(bool(debug_checks))
+    cfg.force_spill = int(bool(force_spill))
+    return cfg
+
+
+class _DevArray:
+    """Zero-copy view of library-owned device memory for torch.as_tensor."""
+
+    def __init__(self, ptr: int, n: int, typestr: str):
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": typestr,
+                                         "data": (ptr, False), "version": 3}
+
+
+class Plan:
+    """A symbolic result (C's pattern and the numeric schedule), library-owned."""
+
+    def __init__(self, handle, dtype_code: int, n: int, m: int):
+        self._h = handle
+        self.dtype_code = dtype_code
+        self.n, self.m = n, m
+        s = self.stats()
+        self.nnz = s["nnz_c"]
+
+    @property
+    def handle(self):
+        if not self._h:
+            raise RuntimeError("plan already destroyed")
+        return self._h
+
+    @property
+    def torch_dtype(self):
+        return torch.float64 if self.dtype_code == F64 else torch.float32
+
+    def pattern(self):
+        """(row_ptr, col_idx) of C as int32 tensors (copies)."""
+        m, nnz = _c.c_int32(), _c.c_int64()
+        rp, ci = _c.c_void_p(), _c.c_void_p()
+        _check(_lib().ptap_plan_pattern(self.handle, _c.byref(m), _c.byref(nnz), _c.byref(rp),
+                                        _c.byref(ci)), "ptap_plan_pattern")
+        dev = torch.device("cuda", torch.cuda.current_device())
+        r = torch.as_tensor(_DevArray(rp.value, m.value + 1, "<i4"), device=dev).clone()
+        c = (torch.as_tensor(_DevArray(ci.value, nnz.value, "<i4"), device=dev).clone()
+             if nnz.value > 0 else torch.zeros(0, dtype=torch.int32, device=dev))
+        return r, c
+
+    def stats(self) -> dict:
+        st = _Stats()
+        _check(_lib().ptap_plan_stats(self.handle, _c.byref(st)), "ptap_plan_stats")
+        return {k: getattr(st, k) for k, _ in _Stats._fields_ if k != "reserved"}
+
+    def check(self, stream=None):
+        _check(_lib().ptap_plan_check(self.handle, _stream(stream)), "device status")
+
+    def destroy(self):
+        if self._h:
+            _lib().ptap_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def symbolic(A: Csr, P: Csr, config: _Config | None = None, stream=None,
+             dtype=None) -> Plan:
+    """ptap_symbolic: pattern of C = P^T A P and the numeric schedule."""
+    code = A.dtype_code if dtype is None else (F64 if dtype == torch.float64 else F32)
+    h = _c.c_void_p()
+    _check(_lib().ptap_symbolic(_c.byref(A.c(code)), _c.byref(P.c(code)),
+                                _c.byref(config) if config is not None else None,
+                                _c.byref(_TORCH_ALLOCATOR), _stream(stream), _c.byref(h)),
+           "ptap_symbolic")
+    return Plan(h, code, A.nrows, P.ncols)
+
+
+def two_step_symbolic(A: Csr, P: Csr, config: _Config | None = None, stream=None,
+                      dtype=None) -> Plan:
+    """ptap_two_step_symbolic: the GPU two-step comparator (holds A P and P^T)."""
+    code = A.dtype_code if dtype is None else (F64 if dtype == torch.float64 else F32)
+    h = _c.c_void_p()
+    _check(_lib().ptap_two_step_symbolic(_c.byref(A.c(code)), _c.byref(P.c(code)),
+                                         _c.byref(config) if config is not None else None,
+                                         _c.byref(_TORCH_ALLOCATOR), _stream(stream),
+                                         _c.byref(h)), "ptap_two_step_symbolic")
+    return Plan(h, code, A.nrows, P.ncols)
+
+
+def numeric(plan: Plan, A: Csr, P: Csr, out: torch.Tensor | None = None, stream=None):
+    """ptap_numeric: values of C on the plan's pattern."""
+    if out is None:
+        out = torch.empty(plan.nnz, dtype=plan.torch_dtype, device=A.row_ptr.device)
+    assert out.is_contiguous() and out.numel() == plan.nnz and out.dtype == plan.torch_dtype
+    _check(_lib().ptap_numeric(plan.handle, _c.byref(A.c()), _c.byref(P.c()), out.data_ptr(),
+                               _stream(stream)), "ptap_numeric")
+    return out
+
+
+def backward(plan: Plan, A: Csr, P: Csr, G: torch.Tensor, need_dA=True, need_dP=True,
+             stream=None):
+    """ptap_backward: (dL/dA on pat(A), dL/dP on pat(P)) given G = dL/dC on pat(C)."""
+    G = G.contiguous()
+    assert G.numel() == plan.nnz and G.dtype == plan.torch_dtype
+    dA = torch.empty(A.nnz, dtype=plan.torch_dtype, device=G.device) if need_dA else None
+    dP = torch.empty(P.nnz, dtype=plan.torch_dtype, device=G.device) if need_dP else None
+    _check(_lib().ptap_backward(plan.handle, _c.byref(A.c()), _c.byref(P.c()), G.data_ptr(),
+                                dA.data_ptr() if dA is not None else None,
+                                dP.data_ptr() if dP is not None else None, _stream(stream)),
+           "ptap_backward")
+    return dA, dP
+
+
+class Batch:
+    """ptap_batch_create / ptap_batch_numeric: many products in one persistent launch."""
+
+    def __init__(self, plans, As, Ps, Cs, stream=None):
+        n = len(plans)
+        self._keep = (list(plans), list(As), list(Ps), list(Cs))
+        hp = (_VP * n)(*[p.handle for p in plans])
+        ca = (_Csr * n)(*[a.c() for a in As])
+        cp = (_Csr * n)(*[p.c() for p in Ps])
+        cc = (_VP * n)(*[c.data_ptr() for c in Cs])
+        h = _c.c_void_p()
+        _check(_lib().ptap_batch_create(hp, ca, cp, cc, n, _c.byref(_TORCH_ALLOCATOR),
+                                        _stream(stream), _c.byref(h)), "ptap_batch_create")
+        self._h = h
+
+    def numeric(self, stream=None):
+        _check(_lib().ptap_batch_numeric(self._h, _stream(stream)), "ptap_batch_numeric")
+
+    def destroy(self):
+        if self._h:
+            _lib().ptap_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+class PtAP(torch.autograd.Function):
+    """C_val = ptap_numeric(plan, A(A_val), P(P_val)), differentiable in A_val and P_val.
+
+    ``plan`` fixes the patterns; A and P carry the index tensors (their
+    ``val`` fields are ignored in favour of the differentiable arguments).
+    """
+
+    @staticmethod
+    def forward(ctx, A_val, P_val, plan: Plan, A: Csr, P: Csr):
+        Aw, Pw = A.with_values(A_val.contiguous()), P.with_values(P_val.contiguous())
+        C = numeric(plan, Aw, Pw)
+        ctx.plan, ctx.A, ctx.P = plan, A, P
+        ctx.save_for_backward(A_val, P_val)
+        return C
+
+    @staticmethod
+    def backward(ctx, G):
+        A_val, P_val = ctx.saved_tensors
+        Aw, Pw = ctx.A.with_values(A_val.contiguous()), ctx.P.with_values(P_val.contiguous())
+        dA, dP = backward(ctx.plan, Aw, Pw, G.contiguous(), ctx.needs_input_grad[0],
+                          ctx.needs_input_grad[1])
+        return dA, dP, None, None, None

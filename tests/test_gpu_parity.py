@@ -1,0 +1,225 @@
+"""CUDA path vs the oracle, element by element, through the C ABI.
+
+Sizes span several chunks and hash tiles and leave ragged tails; configs force
+heavy chunks, tiny on-chip tables (spill / overflow paths) and both numeric
+schemes.  All inputs are seeded.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1905_08423_gb300 import problems as pb
+from paper_1905_08423_gb300 import ptap
+from parity import check_values, rounded, run_and_check, to_dev
+
+pytestmark = pytest.mark.gpu
+
+DTYPES = [torch.float64, torch.float32]
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_model_problem_15(dtype):
+    """15^3 7-point Laplacian, trilinear P: pattern exact, values exact (dyadic)."""
+    A, P = pb.model_problem(15)
+    plan, C = run_and_check(A, P, dtype)
+    ref = oracle.ptap(A, P)
+    np.testing.assert_array_equal(C.cpu().numpy().astype(np.float64), ref.val)
+    assert plan.nnz == 6859
+
+
+@pytest.mark.parametrize("seed", range(8))
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_random_small_int(seed, dtype):
+    """Random patterns with stored zeros and empty rows; integer values are exact."""
+    rng = np.random.default_rng(1000 + seed)
+    n = int(rng.integers(1, 200))
+    m = int(rng.integers(1, 60))
+    A = pb.random_csr(n, n, rng.uniform(0.01, 0.15), rng)
+    P = pb.random_csr(n, m, rng.uniform(0.02, 0.2), rng)
+    plan, C = run_and_check(A, P, dtype)
+    ref = oracle.ptap(A, P)
+    np.testing.assert_array_equal(C.cpu().numpy().astype(np.float64), ref.val)
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_algebraic_20(dtype):
+    """27-point lognormal operator with smoothed aggregation (uneven rows)."""
+    A, P = pb.algebraic_problem(20, seed=3)
+    run_and_check(A, P, dtype)
+
+
+CONFIGS = [
+    dict(),
+    dict(chunk_entries=64),                       # many small chunks
+    dict(chunk_entries=16),                       # every C row heavier than a chunk
+    dict(group_lanes=4), dict(group_lanes=16), dict(group_lanes=32),
+    dict(block_threads=128, group_lanes=8, ap_slots=32),
+    dict(force_spill=True),                       # tiny tables: spill + overflow paths
+    dict(force_spill=True, chunk_entries=64),
+    dict(debug_checks=True),
+    dict(mode=ptap.MODE_ATOMIC),
+    dict(mode=ptap.MODE_ATOMIC, force_spill=True),
+    dict(mode=ptap.MODE_ATOMIC, group_lanes=32),
+]
+
+
+@pytest.mark.parametrize("cfg", CONFIGS, ids=[str(c) for c in CONFIGS])
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_configs(cfg, dtype):
+    A, P = pb.algebraic_problem(13, seed=7)
+    run_and_check(A, P, dtype, ptap.make_config(**cfg))
+    A2, P2 = pb.model_problem(17)
+    run_and_check(A2, P2, dtype, ptap.make_config(**cfg))
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_two_step_comparator(dtype):
+    A, P = pb.algebraic_problem(14, seed=5)
+    plan, C = run_and_check(A, P, dtype, two_step=True)
+    st = plan.stats()
+    assert st["kind"] == 1
+    plan1, C1 = run_and_check(A, P, dtype)
+    # the two-step plan holds A P and P^T: more memory than the all-at-once plan
+    assert st["plan_bytes"] > plan1.stats()["plan_bytes"]
+
+
+def test_edge_cases():
+    # identity P gives A back
+    rng = np.random.default_rng(4)
+    A = pb.random_csr(50, 50, 0.1, rng, int_values=False)
+    plan, C = run_and_check(A, pb.identity_csr(50), torch.float64)
+    np.testing.assert_array_equal(C.cpu().numpy(), A.val)
+    # all P rows empty: C has no entries
+    Pz = pb.CSR(50, 7, np.zeros(51, np.int32), np.zeros(0, np.int32), np.zeros(0))
+    plan, C = run_and_check(A, Pz, torch.float64)
+    assert plan.nnz == 0 and C.numel() == 0
+    # A with no entries
+    Az = pb.CSR(30, 30, np.zeros(31, np.int32), np.zeros(0, np.int32), np.zeros(0))
+    Pr = pb.random_csr(30, 9, 0.3, rng)
+    plan, C = run_and_check(Az, Pr, torch.float64)
+    assert plan.nnz == 0
+    # one-by-one problem
+    one = pb.CSR(1, 1, np.array([0, 1], np.int32), np.array([0], np.int32), np.array([3.0]))
+    plan, C = run_and_check(one, one.with_values(np.array([2.0])), torch.float64)
+    assert C.item() == 12.0
+    # dense-ish rows: a P with a full row and an A row hitting many P rows
+    n, m = 40, 300
+    rp = np.arange(n + 1, dtype=np.int32) * 0
+    cols, vals, lens = [], [], []
+    for i in range(n):
+        c = np.arange(m) if i == 3 else np.sort(rng.choice(m, 5, replace=False))
+        cols.append(c)
+        lens.append(len(c))
+    rp = np.concatenate([[0], np.cumsum(lens)]).astype(np.int32)
+    ci = np.concatenate(cols).astype(np.int32)
+    Pd = pb.CSR(n, m, rp, ci, rng.standard_normal(ci.size))
+    Ad = pb.random_csr(n, n, 0.5, rng, int_values=False)
+    run_and_check(Ad, Pd, torch.float64)
+    run_and_check(Ad, Pd, torch.float32)
+    run_and_check(Ad, Pd, torch.float64, ptap.make_config(chunk_entries=64))
+
+
+def test_errors():
+    A, P = pb.model_problem(7)
+    dA, dP = to_dev(A, torch.float64), to_dev(P, torch.float64)
+    with pytest.raises(ptap.PtapError) as e:
+        ptap.symbolic(dP, dA)   # P is not square
+    assert e.value.code == 1
+    plan = ptap.symbolic(dA, dP)
+    A2, P2 = pb.model_problem(9)
+    with pytest.raises(ptap.PtapError) as e:
+        ptap.numeric(plan, to_dev(A2, torch.float64), to_dev(P2, torch.float64),
+                     out=torch.empty(plan.nnz, dtype=torch.float64, device="cuda"))
+    assert e.value.code == 2
+    # unsorted columns are rejected when checks are on
+    bad = pb.CSR(A.nrows, A.ncols, A.row_ptr, A.col_idx.copy(), A.val)
+    bad.col_idx[1], bad.col_idx[2] = bad.col_idx[2], bad.col_idx[1]
+    with pytest.raises(ptap.PtapError) as e:
+        ptap.symbolic(to_dev(bad, torch.float64), dP, ptap.make_config(debug_checks=True))
+    assert e.value.code == 1
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_backward_vs_oracle(dtype):
+    A, P = pb.poisson2d_problem(64)
+    Pt = pb.perturb_values(P, seed=5)
+    Ar, Pr = rounded(A, dtype), rounded(P, dtype)
+    dA_, dP_ = to_dev(A, dtype), to_dev(P, dtype)
+    plan = ptap.symbolic(dA_, dP_)
+    C = ptap.numeric(plan, dA_, dP_)
+    Ct = ptap.numeric(plan, dA_, to_dev(Pt, dtype))
+    G = 2.0 * (C - Ct)
+    gA, gP = ptap.backward(plan, dA_, dP_, G)
+    torch.cuda.synchronize()
+    Cref = oracle.ptap(Ar, Pr)
+    Gh = pb.CSR(Cref.nrows, Cref.ncols, Cref.row_ptr, Cref.col_idx,
+                G.cpu().numpy().astype(np.float64))
+    eA, eP = oracle.ptap_backward(Ar, Pr, Gh)
+    # bounds: the same products on absolute values
+    absG = Gh.with_values(np.abs(Gh.val))
+    bA, bP = oracle.ptap_backward(Ar.abs(), Pr.abs(), absG)
+    check_values(gA, eA, bA, dtype)
+    check_values(gP, eP, bP, dtype)
+
+
+def test_autograd_function():
+    A, P = pb.poisson2d_problem(32)
+    dA_, dP_ = to_dev(A, torch.float64), to_dev(P, torch.float64)
+    plan = ptap.symbolic(dA_, dP_)
+    Pt = to_dev(pb.perturb_values(P, seed=1), torch.float64)
+    Ct = ptap.numeric(plan, dA_, Pt)
+    Av = dA_.val.clone().requires_grad_(True)
+    Pv = dP_.val.clone().requires_grad_(True)
+    C = ptap.PtAP.apply(Av, Pv, plan, dA_, dP_)
+    loss = ((C - Ct) ** 2).sum()
+    loss.backward()
+    # central differences along a random direction
+    g = torch.Generator(device="cuda").manual_seed(0)
+    v = torch.randn(Pv.shape, generator=g, device="cuda", dtype=torch.float64)
+    h = 1e-6
+    with torch.no_grad():
+        lp = ((ptap.PtAP.apply(Av, Pv + h * v, plan, dA_, dP_) - Ct) ** 2).sum()
+        lm = ((ptap.PtAP.apply(Av, Pv - h * v, plan, dA_, dP_) - Ct) ** 2).sum()
+    fd = (lp - lm).item() / (2 * h)
+    an = (Pv.grad * v).sum().item()
+    assert abs(fd - an) <= 1e-6 * abs(an)
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_batch_and_graph(dtype):
+    probs = pb.batch_problems(seed=4, count=6, lo=8, hi=20)
+    devs, plans, Cs, refs = [], [], [], []
+    for A, P in probs:
+        dA_, dP_ = to_dev(A, dtype), to_dev(P, dtype)
+        plan = ptap.symbolic(dA_, dP_)
+        devs.append((dA_, dP_))
+        plans.append(plan)
+        Cs.append(torch.empty(plan.nnz, dtype=dtype, device="cuda"))
+    batch = ptap.Batch(plans, [d[0] for d in devs], [d[1] for d in devs], Cs)
+    batch.numeric()
+    torch.cuda.synchronize()
+    for (A, P), C in zip(probs, Cs):
+        Ar, Pr = rounded(A, dtype), rounded(P, dtype)
+        check_values(C, oracle.ptap(Ar, Pr).val, oracle.ptap_bound(Ar, Pr).val, dtype)
+    # capture once, rescale A's values in place, replay
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        batch.numeric(stream=s)  # warm-up on the capture stream
+        s.synchronize()
+        with torch.cuda.graph(graph, stream=s):
+            batch.numeric(stream=s)
+    torch.cuda.current_stream().wait_stream(s)
+    for r in range(2):
+        scaled = []
+        for q, (A, P) in enumerate(probs):
+            A2 = pb.rescale_values(A, seed=40 + 10 * r + q)
+            devs[q][0].val.copy_(torch.as_tensor(A2.val, dtype=dtype, device="cuda"))
+            scaled.append(A2)
+        graph.replay()
+        torch.cuda.synchronize()
+        for (A, P), A2, C in zip(probs, scaled, Cs):
+            Ar, Pr = rounded(A2, dtype), rounded(P, dtype)
+            check_values(C, oracle.ptap(Ar, Pr).val, oracle.ptap_bound(Ar, Pr).val, dtype)
