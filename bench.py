@@ -1,0 +1,431 @@
+#!/usr/bin/env python
+"""Benchmark of the all-at-once sparse triple product C = P^T A P on GB300.
+
+Workload: the model problem -- 3D 7-point Laplacian on a 319^3 interior grid
+(32,461,759 rows, 226,621,747 nonzeros) with trilinear interpolation to the
+159^3 coarse grid (4,019,679 columns); C is the 27-point coarse operator
+(107,171,875 nonzeros).  One symbolic product, then repeated numeric products
+(the paper's "one symbolic + eleven numeric").  A step is one numeric product
+with the pattern resident.
+
+Reported (one JSON line on rank 0):
+  value       effective GB/s of the numeric product = algorithmic bytes (A, P,
+              C's pattern read once, C's values written once) / device time
+  roofline    that kernel against the measured HBM copy peak
+  two_step    the GPU two-step comparator on the same input: GB/s and memory
+  peak_mb     device memory of each method (C and workspace, inputs excluded)
+  bwd_fwd     backward / forward time on the 512^2 smoothed-aggregation case
+  e2e         the same metric through the public API with pinned host buffers
+              (A's and P's values in, C's values out, every step)
+  cpu_baseline  the oracle on the host cores, on a slab of fine rows
+Inputs are far larger than L2 (129 MB), so no flush is needed between steps.
+
+--impl reference times the oracle (a plain single-threaded FP64 two-step on
+the host) on the same metric.  --gpus N under torchrun runs one independent
+replica of the workload per GPU (weak scaling, no collective in the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "PtAP numeric GB/s & % HBM roofline vs GPU two-step; peak device MB; bwd/fwd time"
+FP64_FMA_PEAK_G = 505.6  # measured DFMA throughput of one GB300 (GFMA/s), see the design doc
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def alg_bytes(n, nnz_a, m, nnz_p, nnz_c, vb):
+    """Compulsory traffic of one numeric product: A, P and C's pattern read once, C written once."""
+    rd = 4 * (n + 1) + (4 + vb) * nnz_a + 4 * (n + 1) + (4 + vb) * nnz_p + 4 * (m + 1) + 4 * nnz_c
+    return rd + vb * nnz_c
+
+
+def alg_fma(A, P, nnz_c_contrib):
+    lens_p = np.diff(P.row_ptr.astype(np.int64))
+    ap = int(lens_p[A.col_idx].sum())
+    return ap + nnz_c_contrib
+
+
+def ncu_traffic(profile_name: str, src_sha: str):
+    """dram bytes per launch from a committed ncu summary, if it is for this source."""
+    path = os.path.join(ROOT, "profiles", profile_name)
+    try:
+        txt = open(path).read()
+    except OSError:
+        return None
+    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    s = re.search(r"source_sha:\s*([0-9a-f]+)", txt)
+    if not m or not s or s.group(1) != src_sha:
+        return None
+    return float(m.group(1))
+
+
+def kernel_source_sha() -> str:
+    import hashlib
+    h = hashlib.sha1()
+    for f in ("owner.cuh", "numeric.cu", "common.cuh"):
+        with open(os.path.join(ROOT, "paper_1905_08423_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:12]
+
+
+class Clocks:
+    """Samples nvidia-smi every 200 ms; summarises the samples inside a window."""
+
+    Q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+        self.windows = []
+
+    def mark(self):
+        return time.time()
+
+    def stop(self):
+        if self.p:
+            self.p.terminate()
+            self.p.wait()
+
+    def summary(self, t0, t1):
+        self.f.flush()
+        rows = []
+        try:
+            for line in open(self.f.name):
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 10:
+                    continue
+                try:
+                    ts = time.mktime(time.strptime(parts[0].split(".")[0], "%Y/%m/%d %H:%M:%S"))
+                except ValueError:
+                    continue
+                rows.append((ts, parts))
+        except OSError:
+            pass
+        inwin = [p for ts, p in rows if t0 - 1 <= ts <= t1 + 1] or [p for _, p in rows]
+        if not inwin:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(p[2]) for p in inwin if p[2].replace(".", "").isdigit()]
+        mx = [float(p[3]) for p in inwin if p[3].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for p in inwin for k in range(4) if p[6 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(inwin)}
+
+
+def workload_config(size, n, nnz_a, m, nnz_p, nnz_c, ws):
+    return {"workload": f"model problem: {size}^3 7-point Laplacian, trilinear P to "
+                        f"{size // 2}^3 (1 symbolic + repeated numeric)",
+            "n": n, "nnz_a": nnz_a, "m": m, "nnz_p": nnz_p, "nnz_c": nnz_c,
+            "l2": "inputs larger than L2 (no flush)",
+            "parallelism": f"independent replicas x{ws}" if ws > 1 else "single GPU"}
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def run_reference(args, ws, rank):
+    """The oracle (CPU, FP64, single thread) on slabs of fine rows of the same workload."""
+    if rank != 0:
+        return
+    import oracle
+    from paper_1905_08423_gb300 import problems as pb
+    oracle.build()
+    A, P = pb.model_problem(args.size)
+    n, plane = A.nrows, args.size * args.size
+    # calibrate: seconds per fine row on a 4-plane slab
+    t = time.perf_counter()
+    oracle.ptap_row_block(A, P, 0, 4 * plane)
+    per_row = (time.perf_counter() - t) / (4 * plane)
+    budget = max(0.5, min(10.0, 150.0 / max(1, args.steps + args.warmup)))
+    rows = int(min(n, max(plane, budget / per_row)))
+    rows -= rows % plane if rows > plane else 0
+    m = P.ncols
+    # algorithmic bytes scale with the slab's share of the fine rows
+    nnzc = (3 * (args.size // 2) - 2) ** 3
+    total = alg_bytes(n, A.nnz, m, P.nnz, nnzc, 8)
+    frac = rows / n
+    for _ in range(args.warmup):
+        oracle.ptap_row_block(A, P, 0, rows)
+    times = []
+    for _ in range(args.steps):
+        t = time.perf_counter()
+        oracle.ptap_row_block(A, P, 0, rows)
+        times.append(time.perf_counter() - t)
+    sec = sum(times) / len(times)
+    gbs = total * frac / sec / 1e9
+    out = {"impl": "reference", "metric": METRIC, "value": round(gbs, 4), "unit": "GB/s",
+           "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": round(sec * 1e3, 3), "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": workload_config(args.size, n, A.nnz, m, P.nnz, nnzc, ws),
+           "cpu_baseline": {"value": round(gbs, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
+                            "sample": f"fine rows [0, {rows}) of {n}, scaled by their share"},
+           "e2e": {"value": round(gbs, 4), "unit": "GB/s", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def cpu_baseline(A, P, size, nnz_c, target_s=12.0):
+    import oracle
+    oracle.build()
+    n, plane = A.nrows, size * size
+    t = time.perf_counter()
+    oracle.ptap_row_block(A, P, 0, 4 * plane)
+    per_row = (time.perf_counter() - t) / (4 * plane)
+    rows = int(min(n, max(plane, target_s / per_row)))
+    t = time.perf_counter()
+    oracle.ptap_row_block(A, P, 0, rows)
+    sec = time.perf_counter() - t
+    total = alg_bytes(n, A.nnz, P.ncols, P.nnz, nnz_c, 8)
+    gbs = total * (rows / n) / sec / 1e9
+    return {"value": round(gbs, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "sample": f"FP64 two-step oracle on fine rows [0, {rows}) of {n} "
+                      f"({rows / n:.1%}), {sec:.1f} s, bytes scaled by that share"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--size", type=int, default=319)
+    ap.add_argument("--dtype", default="f32", choices=["f32", "f64"])
+    ap.add_argument("--mode", default="owner", choices=["owner", "atomic"])
+    ap.add_argument("--no-extras", action="store_true", help="numeric only (no comparator etc.)")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    ws, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+        return
+
+    import torch
+    import torch.distributed as dist
+    from paper_1905_08423_gb300 import problems as pb
+    from paper_1905_08423_gb300 import ptap
+
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    tdt = torch.float32 if args.dtype == "f32" else torch.float64
+    vb = 4 if args.dtype == "f32" else 8
+
+    A, P = pb.model_problem(args.size)
+    n, m = A.nrows, P.ncols
+    dA = ptap.Csr.from_host(A, dev, tdt)
+    dP = ptap.Csr.from_host(P, dev, tdt)
+    torch.cuda.synchronize()
+    cfg = ptap.make_config(mode=ptap.MODE_OWNER if args.mode == "owner" else ptap.MODE_ATOMIC)
+
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    s = torch.cuda.current_stream()
+
+    # ---- symbolic (once)
+    e0, e1 = ev(), ev()
+    e0.record(s)
+    plan = ptap.symbolic(dA, dP, cfg)
+    e1.record(s)
+    torch.cuda.synchronize()
+    sym_ms = e0.elapsed_time(e1)
+    st = plan.stats()
+    nnz_c = plan.nnz
+    C = torch.empty(nnz_c, dtype=tdt, device=dev)
+    ours_peak = max(st["symbolic_peak_bytes"], st["plan_bytes"] + nnz_c * vb)
+    bytes_step = alg_bytes(n, A.nnz, m, P.nnz, nnz_c, vb)
+
+    # ---- numeric: warm-up, then K timed steps (event per step on the launch stream)
+    for _ in range(args.warmup):
+        ptap.numeric(plan, dA, dP, C)
+    torch.cuda.synchronize()
+    plan.check()
+    clk = Clocks(local)
+    time.sleep(0.6)
+    starts = [ev() for _ in range(args.steps)]
+    ends = [ev() for _ in range(args.steps)]
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t_wall0 = time.time()
+    r0, r1 = ev(), ev()
+    r0.record(s)
+    for k in range(args.steps):
+        starts[k].record(s)
+        ptap.numeric(plan, dA, dP, C)
+        ends[k].record(s)
+    r1.record(s)
+    torch.cuda.synchronize()
+    t_wall1 = time.time()
+    if ws > 1:
+        dist.barrier()
+    region_ms = r0.elapsed_time(r1)
+    per_launch = [a.elapsed_time(b) for a, b in zip(starts, ends)]
+    kern_ms = sum(per_launch) / len(per_launch)
+    if ws > 1:
+        t = torch.tensor([region_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        region_ms = float(t.item())
+    ms_step = region_ms / args.steps
+    value = bytes_step * ws / (ms_step * 1e-3) / 1e9
+    time.sleep(0.3)
+    clocks = clk.summary(t_wall0, t_wall1)
+    clk.stop()
+    plan.check()
+
+    hbm_peak, peak_kind = peaks()
+    achieved = bytes_step / (kern_ms * 1e-3) / 1e9
+    sha = kernel_source_sha()
+    traffic = ncu_traffic(f"numeric_owner_{args.dtype}_model{args.size}.md", sha)
+
+    out = {"metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": ws,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": args.dtype, "data": "synthetic",
+           "config": workload_config(args.size, n, A.nnz, m, P.nnz, nnz_c, ws),
+           "scheme": f"all-at-once, {args.mode} mode",
+           "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak,
+                        "unit": "GB/s", "frac": round(achieved / hbm_peak, 4),
+                        "traffic": traffic, "peak_kind": peak_kind,
+                        "kernel": "k_numeric_owner" if args.mode == "owner" else "k_numeric_atomic",
+                        "alg_bytes_per_launch": bytes_step, "source_sha": sha},
+           "symbolic_ms": round(sym_ms, 2),
+           "c_nnz_per_s": round(nnz_c / (ms_step * 1e-3), 1),
+           "gpu_launches": args.steps,
+           "clocks": clocks}
+
+    if not args.no_extras:
+        # ---- GPU two-step comparator on the same input
+        torch.cuda.synchronize()
+        e0, e1 = ev(), ev()
+        e0.record(s)
+        plan2 = ptap.two_step_symbolic(dA, dP, cfg)
+        e1.record(s)
+        torch.cuda.synchronize()
+        st2 = plan2.stats()
+        C2 = torch.empty(plan2.nnz, dtype=tdt, device=dev)
+        for _ in range(3):
+            ptap.numeric(plan2, dA, dP, C2)
+        k2 = max(3, args.steps // 10)
+        a, b = ev(), ev()
+        a.record(s)
+        for _ in range(k2):
+            ptap.numeric(plan2, dA, dP, C2)
+        b.record(s)
+        torch.cuda.synchronize()
+        plan2.check()
+        two_ms = a.elapsed_time(b) / k2
+        same = bool(torch.allclose(C, C2, rtol=1e-4 if vb == 4 else 1e-10, atol=0))
+        two_peak = max(st2["symbolic_peak_bytes"], st2["plan_bytes"] + plan2.nnz * vb)
+        out["two_step"] = {"value": round(bytes_step / (two_ms * 1e-3) / 1e9, 2), "unit": "GB/s",
+                           "ms_per_step": round(two_ms, 4),
+                           "symbolic_ms": round(e0.elapsed_time(e1), 2),
+                           "speedup_all_at_once": round(two_ms / ms_step, 3),
+                           "agrees_with_all_at_once": same}
+        out["peak_mb"] = {"all_at_once": round(ours_peak / 2**20, 1),
+                          "two_step": round(two_peak / 2**20, 1),
+                          "ratio": round(ours_peak / two_peak, 4),
+                          "c_storage": round((nnz_c * (4 + vb) + 4 * (m + 1)) / 2**20, 1),
+                          "inputs_excluded": True}
+        plan2.destroy()
+        del C2
+        torch.cuda.empty_cache()
+
+        # ---- end to end through the public API with pinned host buffers
+        hA = torch.as_tensor(A.val).to(tdt).pin_memory()
+        hP = torch.as_tensor(P.val).to(tdt).pin_memory()
+        hC = torch.empty(nnz_c, dtype=tdt).pin_memory()
+        for _ in range(2):
+            dA.val.copy_(hA, non_blocking=True)
+            dP.val.copy_(hP, non_blocking=True)
+            ptap.numeric(plan, dA, dP, C)
+            hC.copy_(C, non_blocking=True)
+        ke = max(3, args.steps // 10)
+        a, b = ev(), ev()
+        torch.cuda.synchronize()
+        a.record(s)
+        for _ in range(ke):
+            dA.val.copy_(hA, non_blocking=True)
+            dP.val.copy_(hP, non_blocking=True)
+            ptap.numeric(plan, dA, dP, C)
+            hC.copy_(C, non_blocking=True)
+        b.record(s)
+        torch.cuda.synchronize()
+        e2e_ms = a.elapsed_time(b) / ke
+        out["e2e"] = {"value": round(bytes_step * ws / (e2e_ms * 1e-3) / 1e9, 2), "unit": "GB/s",
+                      "ms_per_step": round(e2e_ms, 3),
+                      "h2d_bytes_per_step": int((A.nnz + P.nnz) * vb),
+                      "d2h_bytes_per_step": int(nnz_c * vb)}
+        del hA, hP, hC
+
+        # ---- backward / forward on the 512^2 smoothed-aggregation case
+        A5, P5 = pb.poisson2d_problem(512)
+        d5A, d5P = ptap.Csr.from_host(A5, dev, tdt), ptap.Csr.from_host(P5, dev, tdt)
+        plan5 = ptap.symbolic(d5A, d5P)
+        C5 = ptap.numeric(plan5, d5A, d5P)
+        G5 = torch.randn_like(C5)
+        for _ in range(5):
+            ptap.numeric(plan5, d5A, d5P, C5)
+            ptap.backward(plan5, d5A, d5P, G5)
+        kb = 50
+        a, b, c = ev(), ev(), ev()
+        a.record(s)
+        for _ in range(kb):
+            ptap.numeric(plan5, d5A, d5P, C5)
+        b.record(s)
+        for _ in range(kb):
+            ptap.backward(plan5, d5A, d5P, G5)
+        c.record(s)
+        torch.cuda.synchronize()
+        fwd, bwd = a.elapsed_time(b) / kb, b.elapsed_time(c) / kb
+        out["bwd_fwd"] = {"ratio": round(bwd / fwd, 3), "fwd_ms": round(fwd, 4),
+                          "bwd_ms": round(bwd, 4), "case": "2D 5-point 512^2, SA 2x2, dA and dP"}
+        plan5.destroy()
+
+        # ---- CPU baseline: the oracle on the host cores (rank 0 only)
+        if rank == 0:
+            out["cpu_baseline"] = cpu_baseline(A, P, args.size, nnz_c)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    plan.destroy()
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()
