@@ -190,6 +190,37 @@ const char* ptap_error_string(int code);
 /* Version of this library as major*10000 + minor*100 + patch. */
 int ptap_version(void);
 
+/* ---- batched numeric products that allocate nothing ---------------------
+ * The paper has no counterpart to this entry point.  It serves callers that
+ * cannot allocate device memory when the products run: solvers that reserve
+ * their whole device footprint in their own pool up front and forbid any
+ * later cudaMalloc, and latency-critical code that cannot afford the implicit
+ * device synchronisation of a cudaMalloc/cudaFree.  Their plans are built
+ * beforehand (ptap_symbolic, which does allocate); this call then runs the
+ * numeric products of `count` plans in one persistent launch, like
+ * ptap_batch_numeric, without creating a batch object.
+ *
+ * Arguments are as for ptap_batch_create: host arrays of `count` plans
+ * (all-at-once plans of one dtype and one configuration), of A and P
+ * descriptors matching each plan, and of caller-owned device buffers for the
+ * values of each C.  The work counter, the problem descriptors and the work
+ * queue live in one file-scope device array of PTAP_NOALLOC_SCRATCH_BYTES
+ * (8 MiB) that every GPU that loads this library holds until the process
+ * exits; the call calls no cudaMalloc, cudaFree or other allocating routine.
+ * The first call on a device looks up that array's device address (once per
+ * device, with the device current); make that first call before any stream
+ * capture.  Every call shares the array and it keeps the last call's
+ * contents: each call clears the work counter itself, and calls whose work
+ * overlaps on the GPU race on the array, so callers must serialise them.
+ * Errors: PTAP_ERR_OVERFLOW when count > PTAP_NOALLOC_MAX_PROBLEMS or the
+ * plans hold more than PTAP_NOALLOC_MAX_ITEMS owner-mode chunks in total;
+ * otherwise as ptap_batch_create.  Asynchronous on `stream`. */
+#define PTAP_NOALLOC_SCRATCH_BYTES (8u << 20)
+#define PTAP_NOALLOC_MAX_PROBLEMS 1024
+#define PTAP_NOALLOC_MAX_ITEMS 1000000
+int ptap_batch_numeric_noalloc(ptap_plan* const* plans, const ptap_csr* A, const ptap_csr* P,
+                               void* const* C_vals, int32_t count, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

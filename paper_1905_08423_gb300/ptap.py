@@ -367,3 +367,24 @@ class PtAP(torch.autograd.Function):
         dA, dP = backward(ctx.plan, Aw, Pw, G.contiguous(), ctx.needs_input_grad[0],
                           ctx.needs_input_grad[1])
         return dA, dP, None, None, None
+
+
+def batch_numeric_noalloc(plans, As, Ps, Cs, stream=None):
+    """ptap_batch_numeric_noalloc: the batched numeric products with no device allocation.
+
+    For callers that cannot allocate device memory while the products run
+    (a fixed device footprint reserved up front, or no room for the implicit
+    synchronisation of an allocation).  The library keeps its work queue in a
+    fixed 8 MiB device array; calls that overlap on the GPU race on it.
+    """
+    L = _lib()
+    f = L.ptap_batch_numeric_noalloc
+    f.argtypes = [_c.POINTER(_VP), _c.POINTER(_Csr), _c.POINTER(_Csr), _c.POINTER(_VP),
+                  _c.c_int32, _VP]
+    n = len(plans)
+    hp = (_VP * n)(*[p.handle for p in plans])
+    ca = (_Csr * n)(*[a.c() for a in As])
+    cp = (_Csr * n)(*[p.c() for p in Ps])
+    cc = (_VP * n)(*[c.data_ptr() for c in Cs])
+    _check(f(hp, ca, cp, cc, n, _stream(stream)), "ptap_batch_numeric_noalloc")
+
