@@ -93,7 +93,12 @@ typedef struct {
   int32_t ap_slots;       /* hash slots per group for one row of A P */
   int32_t debug_checks;   /* nonzero: validate CSR inputs on the device */
   int32_t force_spill;    /* nonzero: shrink on-chip tables to exercise spill paths */
-  int32_t reserved[9];
+  int32_t class_programs; /* 0: run fine rows of one structure class in lockstep from a
+                             per-class program where the patterns allow (owner mode);
+                             -1: always use the general kernel */
+  int32_t visit_block_log2; /* class-program visit order: runs of one class inside blocks
+                               of 2^b consecutive fine rows (0: one block per chunk) */
+  int32_t reserved[7];
 } ptap_config;
 
 /* Statistics of a plan (host struct filled by ptap_plan_stats). */
@@ -110,7 +115,11 @@ typedef struct {
   int32_t mode;              /* numeric scheme the plan uses */
   int32_t chunk_entries, block_threads, group_lanes, ap_slots;
   int32_t kind;              /* 0 all-at-once plan, 1 two-step plan */
-  int32_t reserved[7];
+  int32_t fast_path;         /* 1 if the numeric phase runs per-class programs */
+  int32_t n_classes;         /* distinct fine-row structure classes */
+  int32_t n_segments;        /* same-class runs over all chunks */
+  int32_t n_pieces;          /* warp-sized pieces of those runs */
+  int32_t reserved[3];
 } ptap_stats;
 
 typedef struct ptap_plan ptap_plan;

@@ -17,7 +17,9 @@ Config resolve_config(const ptap_config* c) {
   Config r;
   if (!c) return r;
   if (c->mode == PTAP_MODE_OWNER || c->mode == PTAP_MODE_ATOMIC) r.mode = c->mode;
-  r.chunk_entries = std::min(std::max(pick(c->chunk_entries, r.chunk_entries), 64), 16384);
+  r.chunk_entries = c->chunk_entries > 0 ? std::min(std::max(c->chunk_entries, 64), 16384) : 0;
+  r.class_programs = c->class_programs >= 0 ? 1 : 0;
+  r.visit_block_log2 = (c->visit_block_log2 > 0 && c->visit_block_log2 <= 24) ? c->visit_block_log2 : 0;
   const int bt = pick(c->block_threads, r.block_threads);
   r.block_threads = (bt == 64 || bt == 128 || bt == 256) ? bt : r.block_threads;
   const int g = pick(c->group_lanes, r.group_lanes);
@@ -63,6 +65,10 @@ int ptap_plan_stats(const ptap_plan* p, ptap_stats* o) {
   o->group_lanes = p->cfg.group_lanes;
   o->ap_slots = p->cfg.ap_slots;
   o->kind = p->kind;
+  o->fast_path = p->fast;
+  o->n_classes = p->nclasses;
+  o->n_segments = p->nseg;
+  o->n_pieces = (int32_t)std::min<int64_t>(p->npieces, INT32_MAX);
   return PTAP_OK;
 }
 

@@ -1,0 +1,534 @@
+// Fine-row structure classes for the fast numeric path (symbolic phase).
+//
+// The numeric product is repeated on a fixed symbolic result (Section 4.1:
+// one symbolic, eleven numeric; Section 4.2, Table 8: caching intermediate
+// data).  For a fine row I, everything the numeric phase does except reading
+// values is fixed by the patterns: which P rows the row of A P combines
+// (Alg. 3), which distinct columns that row has, and where each product
+// P(I,i) (A P)(I,j) lands in row i of the preallocated C (Alg. 8).  This file
+// computes that description -- the row's "signature" -- for every fine row,
+// and deduplicates identical signatures into classes.  Operators discretised
+// on meshes have few classes (hundreds), so the numeric kernel can run 32
+// fine rows of one class in lockstep from one small program, with no hashing
+// and no searching.
+//
+// Signature ("program") of fine row I, in the layout the kernel reads:
+//   [0] na  entries of A(I,:)  (<= kFastMaxA)     [1] r  distinct columns of (A P)(I,:) (<= kFastMaxR)
+//   [2] pI  entries of P(I,:)  (<= kFastMaxP)     [3..8) zero
+//   [8 .. 8+A8)      p_a = entries of P(k_a,:), k_a the a-th column of A(I,:); A8 = na rounded up to 8
+//   [.. +8*na)       t(a,b) at a*8+b: slot of P(k_a,:)'s b-th column in the sorted row of A P
+//   [.. +8*r)        sigma at t*8+s: position of the t-th column in C row P(I,:)'s s-th column
+// All padding bytes are zero, so equal rows have byte-equal programs.
+// Rows outside these limits (or with C rows longer than 255) make the plan
+// fall back to the general kernel.
+//
+// Deduplication: a 64-bit hash of each signature goes into an open-addressing
+// table (atomicCAS); the smallest fine row with each hash writes its signature
+// to the program pool; then every row compares its own signature byte by byte
+// with the pool entry of its hash, so a hash collision can only demote rows to
+// the general path, never corrupt results.  No kernel waits on another.
+#include <algorithm>
+
+#include "common.cuh"
+
+namespace ptap {
+
+namespace {
+
+constexpr unsigned long long kEmptyKey = ~0ull;
+
+struct SigGeom {
+  CsrI A, P, C;
+};
+
+// Warp-cooperative signature of fine row I into sig[] (shared memory);
+// returns its length, or -1 if the row is outside the fast-path limits.
+// cand/keys: kFastMaxT ints of shared memory each.
+__device__ int compute_sig(const SigGeom& g, int32_t I, uint8_t* sig, int32_t* cand, int32_t* keys,
+                           int32_t* status) {
+  const int lane = threadIdx.x & 31;
+  const int32_t a0 = g.A.rp[I], na = g.A.rp[I + 1] - a0;
+  const int32_t p0 = g.P.rp[I], pI = g.P.rp[I + 1] - p0;
+  if (na > kFastMaxA || pI > kFastMaxP || pI <= 0) return -1;
+  int32_t pb = 0, pa = 0;
+  if (lane < na) {
+    const int32_t k = g.A.ci[a0 + lane];
+    pb = g.P.rp[k];
+    pa = g.P.rp[k + 1] - pb;
+  }
+  if (__any_sync(0xffffffffu, pa > kFastMaxB)) return -1;
+  int32_t off = pa;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const int32_t y = __shfl_up_sync(0xffffffffu, off, d);
+    if (lane >= d) off += y;
+  }
+  const int32_t T = __shfl_sync(0xffffffffu, off, 31);
+  off -= pa;
+  for (int32_t b = 0; b < pa; ++b) cand[off + b] = g.P.ci[pb + b];
+  // zero the whole program region first (padding must be deterministic)
+  for (int x = lane; x < kFastSigCap; x += 32) sig[x] = 0;
+  __syncwarp();
+  for (int32_t x = lane; x < T; x += 32) keys[x] = cand[x];
+  __syncwarp();
+  // ascending sort of keys[0, T) (bitonic, comparators all ascending)
+  {
+    int p = 1;
+    while (p < T) p <<= 1;
+    for (int size = 2; size <= p; size <<= 1)
+      for (int j = size >> 1; j > 0; j >>= 1) {
+        for (int t = lane; t < (p >> 1); t += 32) {
+          int x, y;
+          if (j == (size >> 1)) {
+            x = (t / j) * size + (t % j);
+            y = (t / j) * size + size - 1 - (t % j);
+          } else {
+            x = (t / j) * 2 * j + (t % j);
+            y = x + j;
+          }
+          if (y < T) {
+            const int32_t kx = keys[x], ky = keys[y];
+            if (kx > ky) {
+              keys[x] = ky;
+              keys[y] = kx;
+            }
+          }
+        }
+        __syncwarp();
+      }
+  }
+  // unique, in place (each 32-wide window is read before it is written)
+  int32_t r = 0, prev = 0;
+  for (int32_t base = 0; base < T; base += 32) {
+    const int32_t x = base + lane;
+    const int32_t kx = x < T ? keys[x] : 0;
+    int32_t up = __shfl_up_sync(0xffffffffu, kx, 1);
+    if (lane == 0) up = prev;
+    const bool first = x < T && (x == 0 || up != kx);
+    const unsigned m = __ballot_sync(0xffffffffu, first);
+    prev = __shfl_sync(0xffffffffu, kx, 31);
+    __syncwarp();
+    if (first) keys[r + __popc(m & ((1u << lane) - 1u))] = kx;
+    r += __popc(m);
+    __syncwarp();
+  }
+  if (r > kFastMaxR) return -1;
+  // slot of each of this lane's products (lane = a, up to kFastMaxB of them)
+  const int A8 = (na + 7) & ~7;
+  const int tsec = 8 + A8;
+  if (lane < na) {
+    sig[8 + lane] = (uint8_t)pa;
+    for (int32_t b = 0; b < pa; ++b) {
+      const int32_t key = cand[off + b];
+      int32_t lo = 0, hi = r;
+      while (lo < hi) {
+        const int32_t mid = (lo + hi) >> 1;
+        if (keys[mid] < key) lo = mid + 1;
+        else hi = mid;
+      }
+      sig[tsec + lane * 8 + b] = (uint8_t)lo;
+    }
+  }
+  const int ssec = tsec + 8 * na;
+  const int tcur = ssec + 8 * r;
+  // positions in the rows of C
+  for (int32_t s = 0; s < pI; ++s) {
+    const int32_t i = g.P.ci[p0 + s];
+    const int32_t c0 = g.C.rp[i], L = g.C.rp[i + 1] - c0;
+    if (L > 255) return -1;
+    if (lane < r) {
+      const int32_t key = keys[lane];
+      int32_t lo = 0, hi = L;
+      while (lo < hi) {
+        const int32_t mid = (lo + hi) >> 1;
+        if (g.C.ci[c0 + mid] < key) lo = mid + 1;
+        else hi = mid;
+      }
+      if (lo >= L || g.C.ci[c0 + lo] != key) atomicExch(status, PTAP_ERR_PATTERN);
+      sig[ssec + lane * 8 + s] = (uint8_t)lo;
+    }
+  }
+  if (lane == 0) {
+    sig[0] = (uint8_t)na;
+    sig[1] = (uint8_t)r;
+    sig[2] = (uint8_t)pI;
+  }
+  __syncwarp();
+  return tcur;
+}
+
+// Length of a program from its header (host and device).
+__host__ __device__ inline int program_length(const uint8_t* g) {
+  return 8 + ((g[0] + 7) & ~7) + 8 * g[0] + 8 * g[1];
+}
+
+__device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+  return z ^ (z >> 31);
+}
+
+// Order-sensitive 64-bit hash of sig[0, len), warp-cooperative.
+__device__ unsigned long long sig_hash(const uint8_t* sig, int len) {
+  const int lane = threadIdx.x & 31;
+  unsigned long long h = 0xcbf29ce484222325ull ^ mix64((unsigned long long)(lane + 1) * 0x9e3779b97f4a7c15ull);
+  for (int x = lane; x < len; x += 32) h = (h ^ (unsigned long long)sig[x]) * 0x100000001b3ull;
+  h = mix64(h + (unsigned long long)lane * 0x632be59bd9b4e019ull + (unsigned long long)len);
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) h ^= __shfl_xor_sync(0xffffffffu, h, d);
+  return h == kEmptyKey ? 0 : h;
+}
+
+struct ClassArgs {
+  SigGeom g;
+  int32_t n;
+  unsigned long long* tkey;  // table keys (hash), kEmptyKey = free
+  int32_t* trep;             // smallest fine row per key
+  int32_t* tcls;             // class id per slot
+  int tlog2;
+  uint8_t* pool;
+  int64_t pool_cap;
+  int32_t* class_off;        // [K+1] pool offset per class (class_off[k] = start)
+  int32_t* counters;         // [0] classes, [1] pool bytes used, [2] slow rows, [3] overflow
+  int32_t* row_class;        // per fine row: class id, or -1 (no P entries), or -2 (general path)
+  int32_t* status;
+};
+
+constexpr int kSigWarps = 4;
+
+struct SigSmem {
+  uint8_t sig[kSigWarps][kFastSigCap];
+  int32_t cand[kSigWarps][kFastMaxT];
+  int32_t keys[kSigWarps][kFastMaxT];
+};
+
+// Phase 1: hash every row's signature into the table.
+__global__ void __launch_bounds__(kSigWarps * 32) k_class_insert(ClassArgs c) {
+  __shared__ SigSmem sm;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t mask = (1u << c.tlog2) - 1u;
+  for (int64_t I = (int64_t)blockIdx.x * kSigWarps + w; I < c.n; I += (int64_t)gridDim.x * kSigWarps) {
+    if (c.g.P.rp[I + 1] == c.g.P.rp[I]) continue;  // never visited
+    const int len = compute_sig(c.g, (int32_t)I, sm.sig[w], sm.cand[w], sm.keys[w], c.status);
+    if (len < 0) {
+      if (lane == 0) atomicAdd(&c.counters[2], 1);
+      continue;
+    }
+    const unsigned long long h = sig_hash(sm.sig[w], len);
+    if (lane == 0) {
+      uint32_t slot = (uint32_t)(h >> 20) & mask;
+      bool done = false;
+      for (uint32_t probe = 0; probe <= mask; ++probe) {
+        const unsigned long long old = atomicCAS(&c.tkey[slot], kEmptyKey, h);
+        if (old == kEmptyKey || old == h) {
+          atomicMin(&c.trep[slot], (int32_t)I);
+          done = true;
+          break;
+        }
+        slot = (slot + 1) & mask;
+      }
+      if (!done) atomicExch(&c.counters[3], 1);
+    }
+    __syncwarp();
+  }
+}
+
+// Phase 2: the representative of every occupied slot writes the pool entry.
+__global__ void __launch_bounds__(kSigWarps * 32) k_class_publish(ClassArgs c) {
+  __shared__ SigSmem sm;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t cap = (int64_t)1 << c.tlog2;
+  for (int64_t slot = (int64_t)blockIdx.x * kSigWarps + w; slot < cap;
+       slot += (int64_t)gridDim.x * kSigWarps) {
+    if (c.tkey[slot] == kEmptyKey) continue;
+    const int32_t I = c.trep[slot];
+    const int len = compute_sig(c.g, I, sm.sig[w], sm.cand[w], sm.keys[w], c.status);
+    int32_t cls = -1, off = 0;
+    if (lane == 0 && len > 0) {
+      off = atomicAdd(&c.counters[1], len);
+      if ((int64_t)off + len <= c.pool_cap) {
+        cls = atomicAdd(&c.counters[0], 1);
+        c.class_off[cls] = off;
+      } else {
+        atomicExch(&c.counters[3], 1);
+      }
+      c.tcls[slot] = cls;
+    }
+    cls = __shfl_sync(0xffffffffu, cls, 0);
+    off = __shfl_sync(0xffffffffu, off, 0);
+    if (cls >= 0)
+      for (int x = lane; x < len; x += 32) c.pool[off + x] = sm.sig[w][x];
+    __syncwarp();
+  }
+}
+
+// Phase 3: every row checks its signature against its class's pool entry.
+__global__ void __launch_bounds__(kSigWarps * 32) k_class_assign(ClassArgs c) {
+  __shared__ SigSmem sm;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t mask = (1u << c.tlog2) - 1u;
+  for (int64_t I = (int64_t)blockIdx.x * kSigWarps + w; I < c.n; I += (int64_t)gridDim.x * kSigWarps) {
+    if (c.g.P.rp[I + 1] == c.g.P.rp[I]) {
+      if (lane == 0) c.row_class[I] = -1;
+      continue;
+    }
+    const int len = compute_sig(c.g, (int32_t)I, sm.sig[w], sm.cand[w], sm.keys[w], c.status);
+    int32_t cls = -2;
+    if (len > 0) {
+      const unsigned long long h = sig_hash(sm.sig[w], len);
+      uint32_t slot = (uint32_t)(h >> 20) & mask;
+      int32_t found = -1;
+      for (uint32_t probe = 0; probe <= mask; ++probe) {
+        const unsigned long long k = c.tkey[slot];
+        if (k == h) {
+          found = c.tcls[slot];
+          break;
+        }
+        if (k == kEmptyKey) break;
+        slot = (slot + 1) & mask;
+      }
+      if (found >= 0) {
+        // lengths first (the header fixes the length), then every byte
+        const uint8_t* ref = c.pool + c.class_off[found];
+        const int rlen = program_length(ref);
+        bool same = rlen == len;
+        if (same)
+          for (int x = lane; x < len; x += 32) same &= (ref[x] == sm.sig[w][x]);
+        same = __all_sync(0xffffffffu, same);
+        if (same) cls = found;
+      }
+    }
+    if (lane == 0) {
+      c.row_class[I] = cls;
+      if (cls == -2) atomicAdd(&c.counters[2], 1);
+    }
+    __syncwarp();
+  }
+}
+
+// Widest span (last - first fine row) of any chunk's ascending visit list.
+__global__ void k_chunk_span(const int32_t* __restrict__ fptr, const int32_t* __restrict__ frows,
+                             int32_t nch, int32_t* maxspan) {
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < nch;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t f0 = fptr[c], f1 = fptr[c + 1];
+    if (f1 > f0) atomicMax(maxspan, frows[f1 - 1] - frows[f0]);
+  }
+}
+
+// Composite sort key (block of 2^bb consecutive fine rows, class, row): runs
+// of one class stay inside a block.  Small blocks make the warps working on a
+// chunk at the same time read neighbouring rows of A and P (L1 reuse); large
+// blocks keep runs long (full warps).  bb is a tuning knob (config).
+__global__ void k_visit_keys(const int32_t* __restrict__ fptr, const int32_t* __restrict__ frows,
+                             int32_t nch, const int32_t* __restrict__ row_class, int shift,
+                             int kBlockBits, int32_t* keys) {
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < nch;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t f0 = fptr[c], f1 = fptr[c + 1];
+    if (f0 == f1) continue;
+    const int32_t base = frows[f0];  // lists are ascending before this sort
+    for (int32_t f = f0; f < f1; ++f) {
+      const int32_t I = frows[f], d = I - base;
+      keys[f] = ((d >> kBlockBits) << (shift + kBlockBits)) | (row_class[I] << kBlockBits) |
+                (d & ((1 << kBlockBits) - 1));
+    }
+  }
+}
+
+__global__ void k_seg_flags(const int32_t* __restrict__ fptr, int32_t nch, const int32_t* __restrict__ keys,
+                            int shift, int kBlockBits, int32_t* flag) {
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < nch;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t f0 = fptr[c], f1 = fptr[c + 1];
+    for (int32_t f = f0; f < f1; ++f)
+      flag[f] = (f == f0 || (keys[f] >> kBlockBits) != (keys[f - 1] >> kBlockBits)) ? 1 : 0;
+  }
+}
+
+__global__ void k_seg_fill(const int32_t* __restrict__ fptr, int32_t nch, const int32_t* __restrict__ keys,
+                           int shift, int kBlockBits, const int32_t* __restrict__ segid, int32_t* seg_ptr,
+                           int32_t* seg_class, int32_t* chunk_seg, int64_t nf) {
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < nch;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t f0 = fptr[c], f1 = fptr[c + 1];
+    chunk_seg[c] = segid[f0];
+    for (int32_t f = f0; f < f1; ++f)
+      if (f == f0 || (keys[f] >> kBlockBits) != (keys[f - 1] >> kBlockBits)) {
+        seg_ptr[segid[f]] = f;
+        seg_class[segid[f]] = (keys[f] >> kBlockBits) & ((1 << shift) - 1);
+      }
+  }
+}
+
+// Pieces: each run split into groups of at most 32 rows (one per warp step).
+__global__ void k_piece_count(const int32_t* __restrict__ seg_ptr, int64_t nseg, int32_t* np) {
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < nseg;
+       g += (int64_t)gridDim.x * blockDim.x)
+    np[g] = (seg_ptr[g + 1] - seg_ptr[g] + 31) >> 5;
+}
+
+__global__ void k_piece_fill(const int32_t* __restrict__ seg_ptr, const int32_t* __restrict__ seg_class,
+                             int64_t nseg, const int32_t* __restrict__ poff, int32_t* piece_f0,
+                             int32_t* piece_meta) {
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < nseg;
+       g += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t f0 = seg_ptr[g], len = seg_ptr[g + 1] - f0;
+    for (int32_t j = 0; j * 32 < len; ++j) {
+      piece_f0[poff[g] + j] = f0 + 32 * j;
+      piece_meta[poff[g] + j] = (seg_class[g] << 6) | min(32, len - 32 * j);
+    }
+  }
+}
+
+__global__ void k_chunk_piece(const int32_t* __restrict__ chunk_seg, int32_t nch,
+                              const int32_t* __restrict__ poff, int32_t* chunk_piece) {
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c <= nch;
+       c += (int64_t)gridDim.x * blockDim.x)
+    chunk_piece[c] = poff[chunk_seg[c]];
+}
+
+}  // namespace
+
+// Builds the classes of the plan's fine rows.  On success with every visited
+// row inside the fast-path limits, sets p->fast and fills the pool, the class
+// offsets and the max slot count; otherwise leaves p->fast = 0.
+int build_classes(ptap_plan* p, const ptap_csr* A, const ptap_csr* P, cudaStream_t s) {
+  p->fast = 0;
+  if (p->n == 0 || p->nnz_c == 0) return PTAP_OK;
+  Scratch sc(&p->mem);
+  const int tlog2 = 16;
+  const int64_t tcap = (int64_t)1 << tlog2;
+  const int64_t pool_cap = (int64_t)1 << 20;
+  unsigned long long* tkey = nullptr;
+  int32_t *trep = nullptr, *tcls = nullptr, *counters = nullptr, *row_class = nullptr;
+  int32_t* class_off = nullptr;
+  uint8_t* pool = nullptr;
+  PTAP_TRY(sc.get(&tkey, tcap));
+  PTAP_TRY(sc.get(&trep, tcap));
+  PTAP_TRY(sc.get(&tcls, tcap));
+  PTAP_TRY(sc.get(&counters, 4));
+  PTAP_TRY(sc.get(&row_class, p->n));
+  PTAP_TRY(sc.get(&class_off, tcap + 1));
+  PTAP_TRY(sc.get(&pool, pool_cap));
+  PTAP_CUDA(cudaMemsetAsync(tkey, 0xff, tcap * sizeof(unsigned long long), s));
+  PTAP_CUDA(cudaMemsetAsync(trep, 0x7f, tcap * sizeof(int32_t), s));
+  PTAP_CUDA(cudaMemsetAsync(counters, 0, 4 * sizeof(int32_t), s));
+  ClassArgs c;
+  c.g = SigGeom{CsrI{A->nrows, A->ncols, A->row_ptr, A->col_idx},
+                CsrI{P->nrows, P->ncols, P->row_ptr, P->col_idx}, CsrI{p->m, p->m, p->c_rp, p->c_ci}};
+  c.n = p->n;
+  c.tkey = tkey;
+  c.trep = trep;
+  c.tcls = tcls;
+  c.tlog2 = tlog2;
+  c.pool = pool;
+  c.pool_cap = pool_cap;
+  c.class_off = class_off;
+  c.counters = counters;
+  c.row_class = row_class;
+  c.status = p->status;
+  const int grid = num_sms() * 8;
+  k_class_insert<<<grid, kSigWarps * 32, 0, s>>>(c);
+  PTAP_LAUNCHED();
+  int32_t h[4];
+  PTAP_CUDA(cudaMemcpyAsync(h, counters, sizeof(h), cudaMemcpyDeviceToHost, s));
+  PTAP_CUDA(cudaStreamSynchronize(s));
+  if (h[2] > 0 || h[3]) return PTAP_OK;  // some row outside the limits, or table full
+  k_class_publish<<<(unsigned)std::min<int64_t>(tcap / kSigWarps, (int64_t)num_sms() * 8), kSigWarps * 32, 0,
+                    s>>>(c);
+  PTAP_LAUNCHED();
+  k_class_assign<<<grid, kSigWarps * 32, 0, s>>>(c);
+  PTAP_LAUNCHED();
+  PTAP_CUDA(cudaMemcpyAsync(h, counters, sizeof(h), cudaMemcpyDeviceToHost, s));
+  PTAP_CUDA(cudaStreamSynchronize(s));
+  if (h[2] > 0 || h[3]) return PTAP_OK;
+  const int32_t K = h[0];
+  const int32_t pool_used = h[1];
+  // composite visit keys need class (bits) + span of each chunk's fine rows
+  int kb = 1;
+  while ((1 << kb) <= K) ++kb;
+  const int shift = kb;  // class field width
+  PTAP_CUDA(cudaMemsetAsync(counters, 0, sizeof(int32_t), s));
+  k_chunk_span<<<grid, 256, 0, s>>>(p->chunk_fptr, p->chunk_frows, p->nchunks, counters);
+  PTAP_LAUNCHED();
+  int32_t maxspan = 0;
+  PTAP_CUDA(cudaMemcpyAsync(&maxspan, counters, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  PTAP_CUDA(cudaStreamSynchronize(s));
+  // key bits: block (d >> bb) | class (kb bits) | d & (2^bb - 1), all below bit 31;
+  // bb defaults to the whole chunk span (class-major order)
+  int kBlockBits = p->cfg.visit_block_log2 > 0 ? p->cfg.visit_block_log2 : 31 - kb;
+  {
+    int need = 0;
+    while (((int64_t)1 << need) <= (int64_t)maxspan) ++need;
+    if (p->cfg.visit_block_log2 <= 0) kBlockBits = std::min(kBlockBits, std::max(need, 1));
+  }
+  if (kBlockBits > 31 - kb) kBlockBits = 31 - kb;
+  if (shift < 1 || kBlockBits < 1 ||
+      ((int64_t)maxspan >> kBlockBits) >= ((int64_t)1 << (31 - kb - kBlockBits)))
+    return PTAP_OK;
+  int32_t *keys = nullptr, *flag = nullptr, *segid = nullptr;
+  PTAP_TRY(sc.get(&keys, p->nfrows));
+  PTAP_TRY(sc.get(&flag, p->nfrows));
+  PTAP_TRY(sc.get(&segid, p->nfrows + 1));
+  k_visit_keys<<<grid, 256, 0, s>>>(p->chunk_fptr, p->chunk_frows, p->nchunks, row_class, shift,
+                                    kBlockBits, keys);
+  PTAP_LAUNCHED();
+  PTAP_TRY(segmented_sort(p->mem, p->chunk_fptr, p->nchunks, keys, p->chunk_frows, -1, s));
+  k_seg_flags<<<grid, 256, 0, s>>>(p->chunk_fptr, p->nchunks, keys, shift, kBlockBits, flag);
+  PTAP_LAUNCHED();
+  int64_t nseg = 0;
+  PTAP_TRY(exclusive_scan(p->mem, flag, segid, p->nfrows, &nseg, s));
+  int32_t *seg_ptr = nullptr, *seg_class = nullptr, *chunk_seg = nullptr, *np = nullptr, *poff = nullptr;
+  PTAP_TRY(sc.get(&seg_ptr, nseg + 1));
+  PTAP_TRY(sc.get(&seg_class, std::max<int64_t>(nseg, 1)));
+  PTAP_TRY(sc.get(&chunk_seg, (int64_t)p->nchunks + 1));
+  k_seg_fill<<<grid, 256, 0, s>>>(p->chunk_fptr, p->nchunks, keys, shift, kBlockBits, segid, seg_ptr,
+                                  seg_class, chunk_seg, p->nfrows);
+  PTAP_LAUNCHED();
+  const int32_t endv[2] = {(int32_t)p->nfrows, (int32_t)nseg};
+  PTAP_CUDA(cudaMemcpyAsync(seg_ptr + nseg, &endv[0], sizeof(int32_t), cudaMemcpyHostToDevice, s));
+  PTAP_CUDA(cudaMemcpyAsync(chunk_seg + p->nchunks, &endv[1], sizeof(int32_t), cudaMemcpyHostToDevice, s));
+  // pieces of at most 32 rows, and each chunk's first piece
+  PTAP_TRY(sc.get(&np, nseg + 1));
+  PTAP_TRY(sc.get(&poff, nseg + 1));
+  k_piece_count<<<grid, 256, 0, s>>>(seg_ptr, nseg, np);
+  PTAP_LAUNCHED();
+  int64_t npieces = 0;
+  PTAP_TRY(exclusive_scan(p->mem, np, poff, nseg, &npieces, s));
+  PTAP_TRY(p->mem.get_n(&p->piece_f0, std::max<int64_t>(npieces, 1)));
+  PTAP_TRY(p->mem.get_n(&p->piece_meta, std::max<int64_t>(npieces, 1)));
+  PTAP_TRY(p->mem.get_n(&p->chunk_piece, (int64_t)p->nchunks + 1));
+  k_piece_fill<<<grid, 256, 0, s>>>(seg_ptr, seg_class, nseg, poff, p->piece_f0, p->piece_meta);
+  PTAP_LAUNCHED();
+  k_chunk_piece<<<grid, 256, 0, s>>>(chunk_seg, p->nchunks, poff, p->chunk_piece);
+  PTAP_LAUNCHED();
+  p->npieces = npieces;
+  // pool and offsets (offsets compacted by class id)
+  PTAP_TRY(p->mem.get_n(&p->class_pool, (int64_t)pool_used + kFastSigCap + 32));
+  PTAP_TRY(p->mem.get_n(&p->class_off, (int64_t)K + 1));
+  PTAP_CUDA(cudaMemcpyAsync(p->class_pool, pool, pool_used, cudaMemcpyDeviceToDevice, s));
+  PTAP_CUDA(cudaMemcpyAsync(p->class_off, class_off, K * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+  // max r over classes decides the kernel variant
+  std::vector<uint8_t> hp(pool_used);
+  std::vector<int32_t> ho(K);
+  PTAP_CUDA(cudaMemcpyAsync(hp.data(), pool, pool_used, cudaMemcpyDeviceToHost, s));
+  PTAP_CUDA(cudaMemcpyAsync(ho.data(), class_off, K * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  PTAP_CUDA(cudaStreamSynchronize(s));
+  int maxr = 0, maxlen = 0, maxa = 0;
+  for (int32_t k = 0; k < K; ++k) {
+    const uint8_t* g = hp.data() + ho[k];
+    maxr = std::max<int>(maxr, g[1]);
+    maxa = std::max<int>(maxa, g[0]);
+    maxlen = std::max(maxlen, program_length(g));
+  }
+  p->nclasses = K;
+  p->nseg = (int32_t)nseg;
+  p->class_maxr = maxr;
+  p->class_maxa = maxa;
+  p->class_maxlen = maxlen;
+  p->fast = 1;
+  return PTAP_OK;
+}
+
+}  // namespace ptap

@@ -126,7 +126,9 @@ struct Scratch {
 // ---------------------------------------------------------------------------
 struct Config {
   int mode = PTAP_MODE_OWNER;
-  int chunk_entries = 4096;
+  int chunk_entries = 0;      // 0: chosen at symbolic time
+  int class_programs = 1;     // fast path by fine-row classes where the patterns allow
+  int visit_block_log2 = 0;   // fast path visit order: blocks of 2^b fine rows (0 = class-major)
   int block_threads = 256;
   int group_lanes = 8;
   int ap_slots = 64;
@@ -186,6 +188,16 @@ struct ptap_plan {
   size_t num_smem = 0;
   int num_per_sm = 0;
 
+  // fine-row classes for the fast numeric path (classes.cu)
+  int fast = 0;
+  int32_t nclasses = 0, nseg = 0, class_maxr = 0, class_maxlen = 0, class_maxa = 0;
+  int64_t npieces = 0;
+  int32_t* piece_f0 = nullptr;    // [npieces] first visit (index into chunk_frows) of each piece
+  int32_t* piece_meta = nullptr;  // [npieces] class << 6 | rows (1..32)
+  int32_t* chunk_piece = nullptr; // [nchunks+1] first piece of each chunk
+  uint8_t* class_pool = nullptr; // class programs (signatures), see classes.cu
+  int32_t* class_off = nullptr;  // [nclasses] offset of each program in the pool
+
   ptap::TwoStepData* two = nullptr;
 };
 
@@ -226,6 +238,15 @@ int transpose_pattern(Tracker& mem, const CsrI& M, int32_t* tp, int32_t* tj,
 // validation of a CSR input (device); returns PTAP_ERR_INVALID on a bad matrix.
 int validate_csr(Tracker& mem, const ptap_csr* M, cudaStream_t s);
 int check_csr_host(const ptap_csr* M, bool need_val);
+
+// limits of the fast path (classes.cu)
+constexpr int kFastMaxA = 32;   // entries of A(I,:)
+constexpr int kFastMaxB = 8;    // entries of each P(k,:) it reaches
+constexpr int kFastMaxT = kFastMaxA * kFastMaxB;
+constexpr int kFastMaxR = 32;   // distinct columns of (A P)(I,:)
+constexpr int kFastMaxP = 8;    // entries of P(I,:)
+constexpr int kFastSigCap = 8 + kFastMaxR + 8 * kFastMaxR + kFastMaxT + 3 * kFastMaxR + 8;  // 656 bytes
+int build_classes(ptap_plan* p, const ptap_csr* A, const ptap_csr* P, cudaStream_t s);
 
 // numeric.cu
 int prepare_numeric(ptap_plan* p);

@@ -215,13 +215,18 @@ static int launch_atomic_g(ptap_plan* p, const NumArgs<V>& a, cudaStream_t s) {
     return PTAP_ERR_INVALID;                                        \
   } while (0)
 
+int prepare_fast(ptap_plan* p);
+int numeric_fast(ptap_plan* p, const ptap_csr* A, const ptap_csr* P, void* C, cudaStream_t s);
+
 int prepare_numeric(ptap_plan* p) {
   if (p->cfg.mode == PTAP_MODE_ATOMIC) PTAP_DISPATCH_VG(p, (prepare_atomic_g<V, G>(p)));
+  if (p->fast) return prepare_fast(p);
   PTAP_DISPATCH_VG(p, (prepare_owner_g<V, G>(p)));
 }
 
 int numeric_owner(ptap_plan* p, const ptap_csr* A, const ptap_csr* P, void* C, cudaStream_t s) {
   if (p->nchunks == 0) return PTAP_OK;
+  if (p->fast) return numeric_fast(p, A, P, C, s);
   PTAP_DISPATCH_VG(p, (launch_owner_g<V, G>(p, make_args<V>(p, A, P, C), s)));
 }
 

@@ -733,7 +733,26 @@ static int symbolic_body(ptap_plan* p, const ptap_csr* A, const ptap_csr* P) {
     p->spill_rows = spilled;
     PTAP_CUDA(cudaStreamSynchronize(s));
   }
+  // Owner-mode schedule.  With per-class programs the on-chip accumulator
+  // needs no column indices, so chunks can be larger (fewer fine rows are
+  // visited by two chunks); without them the general kernel's default applies.
+  const bool user_ch = p->cfg.chunk_entries > 0;
+  const int ch_fast = 8192, ch_general = 4096;
+  const bool try_fast = p->cfg.class_programs && p->cfg.mode == PTAP_MODE_OWNER &&
+                        !p->cfg.force_spill && (!user_ch || p->cfg.chunk_entries >= 256);
+  p->cfg.chunk_entries = user_ch ? p->cfg.chunk_entries : (try_fast ? ch_fast : ch_general);
   PTAP_TRY(build_schedule(p, P, s));
+  if (try_fast) {
+    PTAP_TRY(build_classes(p, A, P, s));
+    if (!p->fast && !user_ch && p->cfg.chunk_entries != ch_general) {
+      p->mem.put(p->chunk_row);
+      p->mem.put(p->chunk_fptr);
+      p->mem.put(p->chunk_frows);
+      p->chunk_row = p->chunk_fptr = p->chunk_frows = nullptr;
+      p->cfg.chunk_entries = ch_general;
+      PTAP_TRY(build_schedule(p, P, s));
+    }
+  }
   PTAP_TRY(prepare_numeric(p));
   PTAP_CUDA(cudaStreamSynchronize(s));
   int32_t st = 0;

@@ -53,7 +53,8 @@ class _Config(_c.Structure):
     _fields_ = [("mode", _c.c_int32), ("chunk_entries", _c.c_int32),
                 ("block_threads", _c.c_int32), ("group_lanes", _c.c_int32),
                 ("ap_slots", _c.c_int32), ("debug_checks", _c.c_int32),
-                ("force_spill", _c.c_int32), ("reserved", _c.c_int32 * 9)]
+                ("force_spill", _c.c_int32), ("class_programs", _c.c_int32),
+                ("visit_block_log2", _c.c_int32), ("reserved", _c.c_int32 * 7)]
 
 
 class _Stats(_c.Structure):
@@ -64,7 +65,9 @@ class _Stats(_c.Structure):
                 ("chunk_fine_rows", _c.c_int64), ("n_spill_rows_symbolic", _c.c_int32),
                 ("mode", _c.c_int32), ("chunk_entries", _c.c_int32),
                 ("block_threads", _c.c_int32), ("group_lanes", _c.c_int32),
-                ("ap_slots", _c.c_int32), ("kind", _c.c_int32), ("reserved", _c.c_int32 * 7)]
+                ("ap_slots", _c.c_int32), ("kind", _c.c_int32), ("fast_path", _c.c_int32),
+                ("n_classes", _c.c_int32), ("n_segments", _c.c_int32),
+                ("n_pieces", _c.c_int32), ("reserved", _c.c_int32 * 3)]
 
 
 _LIB = None
@@ -195,7 +198,8 @@ class Csr:
 
 
 def make_config(mode=MODE_OWNER, chunk_entries=0, block_threads=0, group_lanes=0, ap_slots=0,
-                debug_checks=False, force_spill=False) -> _Config:
+                debug_checks=False, force_spill=False, class_programs=True,
+                visit_block_log2=0) -> _Config:
     cfg = _Config()
     cfg.mode = mode
     cfg.chunk_entries = chunk_entries
@@ -204,6 +208,8 @@ def make_config(mode=MODE_OWNER, chunk_entries=0, block_threads=0, group_lanes=0
     cfg.ap_slots = ap_slots
     cfg.debug_checks = int(bool(debug_checks))
     cfg.force_spill = int(bool(force_spill))
+    cfg.class_programs = 0 if class_programs else -1
+    cfg.visit_block_log2 = visit_block_log2
     return cfg
 
 

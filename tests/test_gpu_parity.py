@@ -61,6 +61,11 @@ CONFIGS = [
     dict(mode=ptap.MODE_ATOMIC),
     dict(mode=ptap.MODE_ATOMIC, force_spill=True),
     dict(mode=ptap.MODE_ATOMIC, group_lanes=32),
+    dict(class_programs=False),                   # general owner kernel
+    dict(chunk_entries=256),                      # class programs, many small chunks
+    dict(chunk_entries=600, block_threads=128),
+    dict(visit_block_log2=6),                     # class programs in 64-row blocks
+    dict(visit_block_log2=8, chunk_entries=2048),
 ]
 
 
@@ -223,3 +228,23 @@ def test_batch_and_graph(dtype):
         for (A, P), A2, C in zip(probs, scaled, Cs):
             Ar, Pr = rounded(A2, dtype), rounded(P, dtype)
             check_values(C, oracle.ptap(Ar, Pr).val, oracle.ptap_bound(Ar, Pr).val, dtype)
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_class_programs_engaged(dtype):
+    """Mesh operators run on per-class programs; results match the oracle and the general kernel."""
+    for A, P in (pb.model_problem(19), pb.algebraic_problem(16, seed=9), pb.poisson2d_problem(40)):
+        plan, C = run_and_check(A, P, dtype)
+        st = plan.stats()
+        assert st["fast_path"] == 1 and st["n_classes"] > 0 and st["n_segments"] >= st["n_chunks"]
+        plan_g, C_g = run_and_check(A, P, dtype, ptap.make_config(class_programs=False))
+        assert plan_g.stats()["fast_path"] == 0
+
+
+def test_class_programs_declined():
+    """Rows beyond the fast-path limits (here: 40 entries in a row of A) use the general kernel."""
+    rng = np.random.default_rng(17)
+    A = pb.random_csr(120, 120, 0.4, rng)
+    P = pb.random_csr(120, 20, 0.1, rng)
+    plan, C = run_and_check(A, P, torch.float64)
+    assert plan.stats()["fast_path"] == 0
