@@ -43,7 +43,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "PtAP numeric GB/s & % HBM roofline vs GPU two-step; peak device MB; bwd/fwd time"
-FP64_FMA_PEAK_G = 505.6  # measured DFMA throughput of one GB300 (GFMA/s), see the design doc
+FP64_FMA_PEAK_G = 505.6  # measured FP64 FMA throughput of one GB300 (GFMA/s), see the design doc
 
 
 def peaks():
@@ -61,10 +61,34 @@ def alg_bytes(n, nnz_a, m, nnz_p, nnz_c, vb):
     return rd + vb * nnz_c
 
 
-def alg_fma(A, P, nnz_c_contrib):
+def alg_fma_model(A, P, size):
+    """FMAs of one product on the model problem: products of A P plus outer-product terms.
+
+    A P: sum over A(I,k) of nnz(P(k,:)).  Outer products: sum over I of
+    nnz(P(I,:)) * nnz((A P)(I,:)); for the 7-point operator with a tensor-
+    product P, the row of A P is Ux*Sy*Sz u Sx*Uy*Sz u Sx*Sy*Uz (S = 1D support
+    of P at the point, U = union over the point and its two neighbours), so
+    its size is |Ux||Sy||Sz| + |Sx||Uy||Sz| + |Sx||Sy||Uz| - 2|Sx||Sy||Sz|.
+    """
     lens_p = np.diff(P.row_ptr.astype(np.int64))
     ap = int(lens_p[A.col_idx].sum())
-    return ap + nnz_c_contrib
+    n = size
+    X = np.arange(1, n + 1)
+    md = n // 2
+    lo = np.where(X % 2 == 0, X // 2, (X - 1) // 2)
+    hi = np.where(X % 2 == 0, X // 2, (X + 1) // 2)
+    lo = np.maximum(lo, 1)
+    hi = np.minimum(hi, md)
+    s1 = hi - lo + 1                      # |S| per 1D point
+    # union over x-1, x, x+1 (neighbours that exist)
+    ulo = np.array([min(lo[max(i - 1, 0):i + 2]) for i in range(n)])
+    uhi = np.array([max(hi[max(i - 1, 0):i + 2]) for i in range(n)])
+    u1 = uhi - ulo + 1
+    sx, ux = s1[None, None, :], u1[None, None, :]
+    sy, uy = s1[None, :, None], u1[None, :, None]
+    sz, uz = s1[:, None, None], u1[:, None, None]
+    r = (ux * sy * sz + sx * uy * sz + sx * sy * uz - 2 * sx * sy * sz).reshape(-1)
+    return ap + int((lens_p * r).sum())
 
 
 def ncu_traffic(profile_name: str, src_sha: str):
@@ -84,7 +108,7 @@ def ncu_traffic(profile_name: str, src_sha: str):
 def kernel_source_sha() -> str:
     import hashlib
     h = hashlib.sha1()
-    for f in ("owner.cuh", "numeric.cu", "common.cuh"):
+    for f in ("owner.cuh", "numeric.cu", "common.cuh", "fastkern.cuh", "fastnum.cu", "jit.cu", "classes.cu"):
         with open(os.path.join(ROOT, "paper_1905_08423_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:12]
@@ -228,6 +252,9 @@ def main():
     ap.add_argument("--dtype", default="f32", choices=["f32", "f64"])
     ap.add_argument("--mode", default="owner", choices=["owner", "atomic"])
     ap.add_argument("--no-extras", action="store_true", help="numeric only (no comparator etc.)")
+    ap.add_argument("--no-tune", action="store_true", help="default launch parameters, no autotuning")
+    ap.add_argument("--config", default=None,
+                    help="launch parameters as JSON (ptap.make_config keywords); skips autotuning")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     ws, rank, local = dist_setup()
@@ -252,7 +279,19 @@ def main():
     dA = ptap.Csr.from_host(A, dev, tdt)
     dP = ptap.Csr.from_host(P, dev, tdt)
     torch.cuda.synchronize()
-    cfg = ptap.make_config(mode=ptap.MODE_OWNER if args.mode == "owner" else ptap.MODE_ATOMIC)
+    tuned = None
+    from paper_1905_08423_gb300 import autotune
+    if args.mode == "atomic":
+        cfg_kw = dict(mode=ptap.MODE_ATOMIC)
+    elif args.config:
+        cfg_kw = json.loads(args.config)
+    elif args.no_tune:
+        cfg_kw = {}
+    else:
+        # launch parameters picked by timing candidates on this problem (not timed below)
+        tuned = autotune.tune(dA, dP, reps=3, warmup=2, cache_path=None, use_cache=False)
+        cfg_kw = dict(tuned.config)
+    cfg = ptap.make_config(**cfg_kw)
 
     ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
     s = torch.cuda.current_stream()
@@ -311,7 +350,15 @@ def main():
     hbm_peak, peak_kind = peaks()
     achieved = bytes_step / (kern_ms * 1e-3) / 1e9
     sha = kernel_source_sha()
-    traffic = ncu_traffic(f"numeric_owner_{args.dtype}_model{args.size}.md", sha)
+    if args.mode == "atomic":
+        kname = "k_numeric_atomic"
+    elif st["fast_path"] and st["n_specialized"]:
+        kname = "ptap_jit_numeric"
+    elif st["fast_path"]:
+        kname = "k_numeric_fast"
+    else:
+        kname = "k_numeric_owner"
+    traffic = ncu_traffic(f"{kname}_{args.dtype}_model{args.size}.md", sha)
 
     out = {"metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": ws,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
@@ -322,8 +369,15 @@ def main():
            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak,
                         "unit": "GB/s", "frac": round(achieved / hbm_peak, 4),
                         "traffic": traffic, "peak_kind": peak_kind,
-                        "kernel": "k_numeric_owner" if args.mode == "owner" else "k_numeric_atomic",
-                        "alg_bytes_per_launch": bytes_step, "source_sha": sha},
+                        "kernel": kname, "alg_bytes_per_launch": bytes_step, "source_sha": sha},
+           "launch_config": {"chosen": cfg_kw, "autotuned": tuned is not None,
+                             "candidates_ms": ([[c, round(m, 4) if isinstance(m, float) else m]
+                                                for c, m in tuned.trials] if tuned else None),
+                             "fast_path": st["fast_path"], "classes": st["n_classes"],
+                             "specialized_classes": st["n_specialized"],
+                             "specialized_share": st["specialized_permille"] / 1000.0,
+                             "chunk_entries": st["chunk_entries"], "chunks": st["n_chunks"],
+                             "fine_row_visits": st["chunk_fine_rows"]},
            "symbolic_ms": round(sym_ms, 2),
            "c_nnz_per_s": round(nnz_c / (ms_step * 1e-3), 1),
            "gpu_launches": args.steps,
@@ -416,6 +470,40 @@ def main():
         out["bwd_fwd"] = {"ratio": round(bwd / fwd, 3), "fwd_ms": round(fwd, 4),
                           "bwd_ms": round(bwd, 4), "case": "2D 5-point 512^2, SA 2x2, dA and dP"}
         plan5.destroy()
+
+        # ---- the same product in FP64: bounded by this part's FP64 FMA rate
+        if args.dtype == "f32":
+            d64A = ptap.Csr.from_host(A, dev, torch.float64)
+            d64P = ptap.Csr.from_host(P, dev, torch.float64)
+            cands = [dict(), dict(specialize=True), dict(chunk_entries=16384, specialize=True)]
+            t64 = autotune.tune(d64A, d64P, candidates=cands, reps=3, warmup=2, cache_path=None,
+                                use_cache=False) if tuned else None
+            plan64 = ptap.symbolic(d64A, d64P, ptap.make_config(**(t64.config if t64 else {})))
+            C64 = torch.empty(plan64.nnz, dtype=torch.float64, device=dev)
+            for _ in range(3):
+                ptap.numeric(plan64, d64A, d64P, C64)
+            k64 = max(5, args.steps // 10)
+            a, b = ev(), ev()
+            a.record(s)
+            for _ in range(k64):
+                ptap.numeric(plan64, d64A, d64P, C64)
+            b.record(s)
+            torch.cuda.synchronize()
+            plan64.check()
+            ms64 = a.elapsed_time(b) / k64
+            fma = alg_fma_model(A, P, args.size)
+            by64 = alg_bytes(n, A.nnz, m, P.nnz, nnz_c, 8)
+            out["f64"] = {"value": round(by64 / (ms64 * 1e-3) / 1e9, 2), "unit": "GB/s",
+                          "ms_per_step": round(ms64, 4),
+                          "hbm_frac": round(by64 / (ms64 * 1e-3) / 1e9 / hbm_peak, 4),
+                          "roofline": {"bound": "alu", "achieved": round(fma / (ms64 * 1e-3) / 1e9, 1),
+                                       "peak": FP64_FMA_PEAK_G, "unit": "GFMA/s",
+                                       "frac": round(fma / (ms64 * 1e-3) / 1e9 / FP64_FMA_PEAK_G, 4),
+                                       "alg_fma_per_launch": fma},
+                          "launch_config": t64.config if t64 else {}}
+            plan64.destroy()
+            del d64A, d64P, C64
+            torch.cuda.empty_cache()
 
         # ---- CPU baseline: the oracle on the host cores (rank 0 only)
         if rank == 0:

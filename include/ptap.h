@@ -98,7 +98,10 @@ typedef struct {
                              -1: always use the general kernel */
   int32_t visit_block_log2; /* class-program visit order: runs of one class inside blocks
                                of 2^b consecutive fine rows (0: one block per chunk) */
-  int32_t reserved[7];
+  int32_t specialize;     /* k > 0: compile straight-line code (NVRTC, at symbolic time) for
+                             at most k classes covering most fine rows; 0 or -1: class
+                             programs are interpreted */
+  int32_t reserved[6];
 } ptap_config;
 
 /* Statistics of a plan (host struct filled by ptap_plan_stats). */
@@ -119,7 +122,9 @@ typedef struct {
   int32_t n_classes;         /* distinct fine-row structure classes */
   int32_t n_segments;        /* same-class runs over all chunks */
   int32_t n_pieces;          /* warp-sized pieces of those runs */
-  int32_t reserved[3];
+  int32_t n_specialized;     /* classes running as compiled straight-line code */
+  int32_t specialized_permille; /* share of fine-row visits they cover, in 1/1000 */
+  int32_t specialize_us;     /* time spent generating and compiling that code */
 } ptap_stats;
 
 typedef struct ptap_plan ptap_plan;

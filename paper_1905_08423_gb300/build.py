@@ -23,7 +23,22 @@ LIB = os.path.join(OUT, "libptap.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xptxas", "-O3",
-         "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]
+         "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC, "-I", OUT]
+# Device header that the library also hands to NVRTC at run time (jit.cu).
+JIT_HEADER = os.path.join(CSRC, "fastkern.cuh")
+JIT_INC = os.path.join(OUT, "fastkern_src.inc")
+
+
+def _embed_jit_header() -> None:
+    """Writes fastkern.cuh into a C string literal that jit.cu compiles in."""
+    if not _stale(JIT_INC, [JIT_HEADER]):
+        return
+    text = open(JIT_HEADER).read()
+    assert ")PTAPSRC\"" not in text
+    tmp = JIT_INC + f".{os.getpid()}.tmp"
+    with open(tmp, "w") as f:
+        f.write('static const char kFastKernSource[] = R"PTAPSRC(' + text + ')PTAPSRC";\n')
+    os.replace(tmp, JIT_INC)
 
 
 def nvcc() -> str:
@@ -47,8 +62,9 @@ def _stale(target: str, sources: list[str]) -> bool:
 def build(verbose: bool = False, extra: list[str] | None = None) -> str:
     """Compile (if stale) and return the path of libptap.so."""
     os.makedirs(OUT, exist_ok=True)
+    _embed_jit_header()
     sources = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
-    deps = _deps()
+    deps = _deps() + [JIT_INC]
     cc = nvcc()
     extra = list(extra or [])
     jobs = []
@@ -74,7 +90,7 @@ def build(verbose: bool = False, extra: list[str] | None = None) -> str:
             list(ex.map(run, jobs))
     if _stale(LIB, objs):
         tmp = LIB + f".{os.getpid()}.tmp"
-        run([cc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"])
+        run([cc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart", "-ldl"])
         os.replace(tmp, LIB)
     return LIB
 

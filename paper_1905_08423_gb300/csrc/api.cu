@@ -20,6 +20,8 @@ Config resolve_config(const ptap_config* c) {
   r.chunk_entries = c->chunk_entries > 0 ? std::min(std::max(c->chunk_entries, 64), 16384) : 0;
   r.class_programs = c->class_programs >= 0 ? 1 : 0;
   r.visit_block_log2 = (c->visit_block_log2 > 0 && c->visit_block_log2 <= 24) ? c->visit_block_log2 : 0;
+  r.jit = c->specialize > 0 ? 1 : 0;
+  if (c->specialize > 0) r.jit_max_classes = std::min(c->specialize, 256);
   const int bt = pick(c->block_threads, r.block_threads);
   r.block_threads = (bt == 64 || bt == 128 || bt == 256) ? bt : r.block_threads;
   const int g = pick(c->group_lanes, r.group_lanes);
@@ -69,6 +71,9 @@ int ptap_plan_stats(const ptap_plan* p, ptap_stats* o) {
   o->n_classes = p->nclasses;
   o->n_segments = p->nseg;
   o->n_pieces = (int32_t)std::min<int64_t>(p->npieces, INT32_MAX);
+  o->n_specialized = p->jit_fn ? p->jit_classes : 0;
+  o->specialized_permille = p->jit_fn ? (int32_t)(p->jit_coverage * 1000.0 + 0.5) : 0;
+  o->specialize_us = (int32_t)std::min(p->jit_ms * 1000.0, 2.0e9);
   return PTAP_OK;
 }
 

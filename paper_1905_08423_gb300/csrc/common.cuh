@@ -129,6 +129,8 @@ struct Config {
   int chunk_entries = 0;      // 0: chosen at symbolic time
   int class_programs = 1;     // fast path by fine-row classes where the patterns allow
   int visit_block_log2 = 0;   // fast path visit order: blocks of 2^b fine rows (0 = class-major)
+  int jit = 0;                // specialise the most frequent classes with NVRTC
+  int jit_max_classes = 32;
   int block_threads = 256;
   int group_lanes = 8;
   int ap_slots = 64;
@@ -195,6 +197,11 @@ struct ptap_plan {
   int32_t* piece_f0 = nullptr;    // [npieces] first visit (index into chunk_frows) of each piece
   int32_t* piece_meta = nullptr;  // [npieces] class << 6 | rows (1..32)
   int32_t* chunk_piece = nullptr; // [nchunks+1] first piece of each chunk
+
+  // plan-time specialised kernel (jit.cu); null when the interpreter runs
+  void* jit_fn = nullptr;
+  int jit_per_sm = 0, jit_classes = 0;
+  double jit_coverage = 0.0, jit_ms = 0.0;
   uint8_t* class_pool = nullptr; // class programs (signatures), see classes.cu
   int32_t* class_off = nullptr;  // [nclasses] offset of each program in the pool
 

@@ -1,0 +1,187 @@
+// Device code of the class-program numeric kernel (owner mode, fast path).
+//
+// This header is compiled twice: by nvcc into libptap (the interpreter kernel
+// k_numeric_fast) and, at symbolic time, by NVRTC together with generated
+// straight-line code for the plan's most frequent classes (jit.cu).  It
+// therefore includes no system header under NVRTC and holds device code only.
+//
+// The product (Section 3, Eq. 9, Alg. 8): a CTA owns a chunk of coarse rows,
+// accumulates C's values for it on chip and writes them once.  The fine rows
+// visiting the chunk come in pieces of at most 32 rows of one structure
+// class; a warp runs one piece, one row per lane:
+//
+//   R(t) += A(I,k_a) P(k_a, b)            for each product (a, b)       (Alg. 3)
+//   C(i_s, sigma(s,t)) += P(I,i_s) R(t)    for i_s inside the chunk     (Alg. 8)
+//
+// Program layout (bytes, see classes.cu): [0] na, [1] r, [2] pI, [8..8+A8)
+// p_a, then t(a,b) at a*8+b, then sigma at t*8+s.
+#pragma once
+
+#ifdef __CUDACC_RTC__
+typedef int int32_t;
+typedef unsigned int uint32_t;
+typedef long long int64_t;
+typedef unsigned long long uint64_t;
+typedef unsigned char uint8_t;
+typedef decltype(sizeof(0)) size_t;
+#else
+#include <stdint.h>
+#endif
+
+namespace ptapk {
+
+constexpr int kMaxB = 8;  // entries of each P(k,:) a class may reach
+constexpr int kMaxP = 8;  // entries of P(I,:)
+
+template <typename V>
+struct FCsr {
+  int32_t nrows, ncols;
+  const int32_t* rp;
+  const int32_t* ci;
+  const V* val;
+};
+
+template <typename V>
+struct FastArgs {
+  FCsr<V> A, P;
+  const int32_t* c_rp;
+  V* c_val;
+  const int32_t* chunk_row;
+  const int32_t* chunk_piece;
+  const int32_t* piece_f0;
+  const int32_t* piece_meta;  // class << 6 | rows
+  const int32_t* frows;
+  const uint8_t* pool;
+  const int32_t* class_off;
+  int32_t nchunks;
+  int32_t CH;
+  int32_t max_rows;
+  int32_t prog_cap;  // bytes of program buffer per warp (multiple of 16)
+  int32_t maxr;      // largest row of A P over the classes
+};
+
+// Interpreter: 32 fine rows [f, min(f+32, f1)) of one class, one per lane.
+// R is the lane's row of A P, lane-major in shared memory (R[t*32 + lane]).
+template <typename V>
+__device__ __forceinline__ void fast_piece(const FastArgs<V>& a, const uint8_t* prog, V* R, int32_t f,
+                                           int32_t f1, int32_t i0, int32_t i1, V* acc,
+                                           const int32_t* roff) {
+  const int lane = threadIdx.x & 31;
+  const bool valid = f + lane < f1;
+  // lanes past the piece's end redo its first row and add nothing
+  const int32_t I = a.frows[valid ? f + lane : f];
+  const int na = prog[0], r = prog[1], pI = prog[2];
+  const uint8_t* pa_sec = prog + 8;
+  const uint64_t* t_sec = (const uint64_t*)(prog + 8 + ((na + 7) & ~7));
+  const uint64_t* s_sec = t_sec + na;
+  for (int t = 0; t < r; ++t) R[t * 32 + lane] = V(0);
+  // row of A P (Alg. 3), four entries of A(I,:) at a time
+  const int32_t ra = a.A.rp[I];
+  for (int x0 = 0; x0 < na; x0 += 4) {
+    int32_t k[4];
+    V av[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      if (x0 + j < na) {
+        k[j] = a.A.ci[ra + x0 + j];
+        av[j] = a.A.val[ra + x0 + j];
+      }
+    int32_t pb[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      if (x0 + j < na) pb[j] = a.P.rp[k[j]];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if (x0 + j >= na) break;
+      const int pa = pa_sec[x0 + j];
+      const uint64_t tw = t_sec[x0 + j];
+      V v[kMaxB];
+#pragma unroll
+      for (int b = 0; b < kMaxB; ++b)
+        if (b < pa) v[b] = a.P.val[pb[j] + b];
+#pragma unroll
+      for (int b = 0; b < kMaxB; ++b) {
+        if (b >= pa) break;
+        const int t = (int)((tw >> (8 * b)) & 0xff);
+        R[t * 32 + lane] += av[j] * v[b];
+      }
+    }
+  }
+  // outer product with P(I,:) into the chunk (Alg. 8)
+  const int32_t rp = a.P.rp[I];
+  int32_t cb[kMaxP];
+  V ws[kMaxP];
+#pragma unroll
+  for (int s = 0; s < kMaxP; ++s) {
+    cb[s] = -1;
+    ws[s] = V(0);
+    if (s < pI) {
+      const int32_t i = a.P.ci[rp + s];
+      ws[s] = a.P.val[rp + s];
+      if (valid && i >= i0 && i < i1) cb[s] = roff[i - i0];
+    }
+  }
+  for (int t = 0; t < r; ++t) {
+    const V rt = R[t * 32 + lane];
+    const uint64_t sw = s_sec[t];
+#pragma unroll
+    for (int s = 0; s < kMaxP; ++s) {
+      if (s >= pI) break;
+      if (cb[s] >= 0) atomicAdd(&acc[cb[s] + (int)((sw >> (8 * s)) & 0xff)], ws[s] * rt);
+    }
+  }
+}
+
+// Shared-memory carve-up: accumulator | interpreter R rows | row offsets |
+// per-warp program buffers; every region 16-byte aligned.
+template <typename V>
+__host__ __device__ inline size_t fast_smem_bytes(int CH, int threads, int maxr, int max_rows,
+                                                  int prog_cap) {
+  const int CHa = (CH + 3) & ~3;
+  const int rows = (max_rows + 1 + 3) & ~3;
+  return ((size_t)CHa + (size_t)threads * maxr) * sizeof(V) + (size_t)rows * 4 +
+         (size_t)(threads / 32) * prog_cap;
+}
+
+// The kernel body.  `special(a, cls, f, f1, i0, i1, acc, roff)` runs a piece
+// of a class it has straight-line code for and returns true; otherwise the
+// interpreter runs it from the class's program.
+template <typename V, typename Special>
+__device__ __forceinline__ void fast_kernel_body(const FastArgs<V>& a, Special special) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+  const int CHa = (a.CH + 3) & ~3;
+  V* acc = (V*)smraw;
+  V* Rs = acc + CHa + (size_t)warp * 32 * a.maxr;
+  int32_t* roff = (int32_t*)(acc + CHa + (size_t)nwarps * 32 * a.maxr);
+  uint8_t* progs = (uint8_t*)(roff + ((a.max_rows + 1 + 3) & ~3));
+  uint8_t* prog = progs + warp * a.prog_cap;
+  for (int32_t c = blockIdx.x; c < a.nchunks; c += gridDim.x) {
+    const int32_t i0 = a.chunk_row[c], i1 = a.chunk_row[c + 1];
+    const int32_t base = a.c_rp[i0], nnz = a.c_rp[i1] - base;
+    for (int t = threadIdx.x; t < nnz; t += blockDim.x) acc[t] = V(0);
+    for (int t = threadIdx.x; t <= i1 - i0; t += blockDim.x) roff[t] = a.c_rp[i0 + t] - base;
+    __syncthreads();
+    // the chunk's pieces (<= 32 rows of one class) go round-robin to the warps
+    int32_t loaded = -1;
+    const int32_t pe = a.chunk_piece[c + 1];
+    for (int32_t pc = a.chunk_piece[c] + warp; pc < pe; pc += nwarps) {
+      const int32_t meta = a.piece_meta[pc], f0 = a.piece_f0[pc];
+      const int32_t cls = meta >> 6, f1 = f0 + (meta & 63);
+      if (special(a, cls, f0, f1, i0, i1, acc, roff)) continue;
+      if (cls != loaded) {
+        __syncwarp();
+        const uint8_t* src = a.pool + a.class_off[cls];
+        for (int x = lane; x < a.prog_cap; x += 32) prog[x] = src[x];
+        __syncwarp();
+        loaded = cls;
+      }
+      fast_piece<V>(a, prog, Rs, f0, f1, i0, i1, acc, roff);
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < nnz; t += blockDim.x) a.c_val[base + t] = acc[t];
+    __syncthreads();
+  }
+}
+
+}  // namespace ptapk

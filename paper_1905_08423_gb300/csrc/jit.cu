@@ -1,0 +1,267 @@
+// Plan-time specialisation of the class-program kernel.
+//
+// The interpreter in fastkern.cuh decodes each class's program (which product
+// goes to which slot of the row of A P, and where each outer-product term
+// lands in C) at run time.  For the classes that carry most of a plan's fine
+// rows this file writes the same computation as straight-line CUDA -- slots
+// become registers, positions become immediate offsets, and each coarse row
+// of P(I,:) gets one guarded block of accumulations -- compiles it for sm_103a
+// with NVRTC together with fastkern.cuh, and loads it.  Other classes still
+// run on the interpreter inside the same kernel.  Nothing here changes what is
+// computed: the generated code performs the products of the program in the
+// interpreter's order.
+//
+// NVRTC and the driver API are reached through dlopen and the runtime's
+// driver entry points, so the library loads (and simply runs the interpreter)
+// where either is missing.  Compiled modules are kept for the life of the
+// process, keyed by device and source, and shared between plans.
+#include <cuda.h>
+#include <dlfcn.h>
+#include <nvrtc.h>
+
+#include <algorithm>
+#include <chrono>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "fastkern.cuh"
+#include "fastkern_src.inc"  // kFastKernSource: the text of fastkern.cuh
+
+namespace ptap {
+
+size_t fast_smem_for(const ptap_plan* p);
+
+namespace {
+
+struct Nvrtc {
+  bool ok = false;
+  decltype(&nvrtcCreateProgram) create = nullptr;
+  decltype(&nvrtcCompileProgram) compile = nullptr;
+  decltype(&nvrtcGetProgramLogSize) log_size = nullptr;
+  decltype(&nvrtcGetProgramLog) log = nullptr;
+  decltype(&nvrtcGetCUBINSize) cubin_size = nullptr;
+  decltype(&nvrtcGetCUBIN) cubin = nullptr;
+  decltype(&nvrtcDestroyProgram) destroy = nullptr;
+};
+
+struct Driver {
+  bool ok = false;
+  decltype(&cuModuleLoadData) load = nullptr;
+  decltype(&cuModuleGetFunction) get_fn = nullptr;
+  decltype(&cuFuncSetAttribute) set_attr = nullptr;
+  decltype(&cuOccupancyMaxActiveBlocksPerMultiprocessor) occupancy = nullptr;
+  decltype(&cuLaunchKernel) launch = nullptr;
+};
+
+std::mutex g_mu;
+Nvrtc g_rtc;
+Driver g_drv;
+bool g_loaded = false;
+std::map<std::pair<int, uint64_t>, CUfunction> g_cache;  // (device, source hash) -> function
+
+template <class F>
+bool sym(void* lib, const char* name, F& f) {
+  f = (F)dlsym(lib, name);
+  return f != nullptr;
+}
+
+template <class F>
+bool drv(const char* name, F& f) {
+  void* p = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  if (cudaGetDriverEntryPointByVersion(name, &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+      q != cudaDriverEntryPointSuccess || !p) {
+    cudaGetLastError();
+    return false;
+  }
+  f = (F)p;
+  return true;
+}
+
+void load_apis() {
+  if (g_loaded) return;
+  g_loaded = true;
+  void* lib = nullptr;
+  for (const char* n : {"libnvrtc.so.13", "libnvrtc.so", "/usr/local/cuda/lib64/libnvrtc.so"})
+    if ((lib = dlopen(n, RTLD_NOW | RTLD_LOCAL))) break;
+  if (lib)
+    g_rtc.ok = sym(lib, "nvrtcCreateProgram", g_rtc.create) && sym(lib, "nvrtcCompileProgram", g_rtc.compile) &&
+               sym(lib, "nvrtcGetProgramLogSize", g_rtc.log_size) && sym(lib, "nvrtcGetProgramLog", g_rtc.log) &&
+               sym(lib, "nvrtcGetCUBINSize", g_rtc.cubin_size) && sym(lib, "nvrtcGetCUBIN", g_rtc.cubin) &&
+               sym(lib, "nvrtcDestroyProgram", g_rtc.destroy);
+  g_drv.ok = drv("cuModuleLoadData", g_drv.load) && drv("cuModuleGetFunction", g_drv.get_fn) &&
+             drv("cuFuncSetAttribute", g_drv.set_attr) &&
+             drv("cuOccupancyMaxActiveBlocksPerMultiprocessor", g_drv.occupancy) &&
+             drv("cuLaunchKernel", g_drv.launch);
+}
+
+uint64_t fnv64(const std::string& s) {
+  uint64_t h = 0xcbf29ce484222325ull;
+  for (unsigned char c : s) h = (h ^ c) * 0x100000001b3ull;
+  return h;
+}
+
+// Straight-line code for one class program g (layout in fastkern.cuh).
+std::string gen_class(int cls, const uint8_t* g) {
+  const int na = g[0], r = g[1], pI = g[2];
+  const uint8_t* pa = g + 8;
+  const uint8_t* tsec = g + 8 + ((na + 7) & ~7);
+  const uint8_t* ssec = tsec + 8 * na;
+  std::string o;
+  char buf[256];
+  snprintf(buf, sizeof buf,
+           "__device__ __forceinline__ void cls_%d(const FastArgs<V>& a, int32_t f, int32_t f1, int32_t i0,"
+           " int32_t i1, V* acc, const int32_t* roff) {\n",
+           cls);
+  o += buf;
+  o += "  const int lane = threadIdx.x & 31;\n  const bool valid = f + lane < f1;\n"
+       "  const int32_t I = a.frows[valid ? f + lane : f];\n  const int32_t ra = a.A.rp[I];\n"
+       "  const int32_t* Aci = a.A.ci + ra;\n  const V* Av = a.A.val + ra;\n  const V* Pv = a.P.val;\n";
+  for (int x = 0; x < na; ++x) {
+    snprintf(buf, sizeof buf, "  const V a%d = Av[%d];\n  const int32_t q%d = a.P.rp[Aci[%d]];\n", x, x, x, x);
+    o += buf;
+  }
+  // slots of the row of A P, products summed in the interpreter's (a, b) order
+  for (int t = 0; t < r; ++t) {
+    bool first = true;
+    snprintf(buf, sizeof buf, "  V R%d = V(0);\n", t);
+    o += buf;
+    for (int x = 0; x < na; ++x)
+      for (int b = 0; b < pa[x]; ++b)
+        if (tsec[x * 8 + b] == t) {
+          snprintf(buf, sizeof buf, "  R%d += a%d * Pv[q%d + %d];\n", t, x, x, b);
+          o += buf;
+          first = false;
+        }
+    (void)first;
+  }
+  o += "  const int32_t rp = a.P.rp[I];\n";
+  for (int s = 0; s < pI; ++s) {
+    snprintf(buf, sizeof buf,
+             "  { const int32_t i = a.P.ci[rp + %d]; const V w = a.P.val[rp + %d];\n"
+             "    if (valid && i >= i0 && i < i1) { V* c = acc + roff[i - i0];\n",
+             s, s);
+    o += buf;
+    for (int t = 0; t < r; ++t) {
+      snprintf(buf, sizeof buf, "      atomicAdd(c + %d, w * R%d);\n", (int)ssec[t * 8 + s], t);
+      o += buf;
+    }
+    o += "    } }\n";
+  }
+  o += "}\n";
+  return o;
+}
+
+}  // namespace
+
+// Picks the classes with the most visited rows, generates and compiles the
+// specialised kernel.  Returns PTAP_OK with p->jit_fn set, or any error (the
+// caller then keeps the interpreter).
+int jit_prepare(ptap_plan* p) {
+  std::lock_guard<std::mutex> lock(g_mu);
+  load_apis();
+  if (!g_rtc.ok || !g_drv.ok || !p->fast || p->nclasses <= 0) return PTAP_ERR_UNSUPPORTED;
+  cudaStream_t s = p->stream;
+  // visits per class, from the pieces
+  std::vector<int32_t> meta(p->npieces), off(p->nclasses);
+  PTAP_CUDA(cudaMemcpyAsync(meta.data(), p->piece_meta, meta.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  PTAP_CUDA(cudaMemcpyAsync(off.data(), p->class_off, off.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  std::vector<int64_t> visits(p->nclasses, 0);
+  int64_t total = 0;
+  int pool_len = 0;
+  PTAP_CUDA(cudaStreamSynchronize(s));
+  for (int32_t m : meta) {
+    visits[m >> 6] += m & 63;
+    total += m & 63;
+  }
+  for (int32_t o : off) pool_len = std::max(pool_len, o + p->class_maxlen);
+  std::vector<uint8_t> pool(pool_len);
+  PTAP_CUDA(cudaMemcpy(pool.data(), p->class_pool, pool_len, cudaMemcpyDeviceToHost));
+  std::vector<int> order(p->nclasses);
+  for (int k = 0; k < p->nclasses; ++k) order[k] = k;
+  std::sort(order.begin(), order.end(), [&](int x, int y) { return visits[x] > visits[y]; });
+  std::vector<int> hot;
+  int64_t covered = 0;
+  for (int k : order) {
+    if ((int)hot.size() >= p->cfg.jit_max_classes || covered >= total * 99 / 100 || visits[k] == 0) break;
+    hot.push_back(k);
+    covered += visits[k];
+  }
+  if (hot.empty()) return PTAP_ERR_UNSUPPORTED;
+  std::sort(hot.begin(), hot.end());
+  // source
+  std::string src = "#include \"fastkern.cuh\"\nusing namespace ptapk;\n";
+  src += p->dtype == PTAP_F64 ? "typedef double V;\n" : "typedef float V;\n";
+  for (int k : hot) src += gen_class(k, pool.data() + off[k]);
+  src += "struct Special {\n  __device__ bool operator()(const FastArgs<V>& a, int32_t cls, int32_t f, int32_t f1,"
+         " int32_t i0, int32_t i1, V* acc, const int32_t* roff) const {\n    switch (cls) {\n";
+  for (int k : hot) {
+    char buf[160];
+    snprintf(buf, sizeof buf, "      case %d: cls_%d(a, f, f1, i0, i1, acc, roff); return true;\n", k, k);
+    src += buf;
+  }
+  src += "      default: return false;\n    }\n  }\n};\n"
+         "extern \"C\" __global__ void __launch_bounds__(256) ptap_jit_numeric(FastArgs<V> a) {\n"
+         "  fast_kernel_body<V>(a, Special());\n}\n";
+  int dev = 0;
+  PTAP_CUDA(cudaGetDevice(&dev));
+  const uint64_t key = fnv64(src) ^ fnv64(kFastKernSource);
+  CUfunction fn = nullptr;
+  auto it = g_cache.find({dev, key});
+  const auto t0 = std::chrono::steady_clock::now();
+  if (it != g_cache.end()) {
+    fn = it->second;
+  } else {
+    nvrtcProgram prog;
+    const char* hdr[1] = {kFastKernSource};
+    const char* hname[1] = {"fastkern.cuh"};
+    if (g_rtc.create(&prog, src.c_str(), "ptap_jit.cu", 1, hdr, hname) != NVRTC_SUCCESS) return PTAP_ERR_CUDA;
+    const char* opts[] = {"--gpu-architecture=sm_103a", "-std=c++17", "-lineinfo"};
+    const nvrtcResult rc = g_rtc.compile(prog, 3, opts);
+    if (rc != NVRTC_SUCCESS) {
+      if (getenv("PTAP_VERBOSE")) {
+        size_t n = 0;
+        g_rtc.log_size(prog, &n);
+        std::string log(n, '\0');
+        g_rtc.log(prog, &log[0]);
+        fprintf(stderr, "ptap: NVRTC failed:\n%s\n", log.c_str());
+      }
+      g_rtc.destroy(&prog);
+      return PTAP_ERR_CUDA;
+    }
+    size_t n = 0;
+    g_rtc.cubin_size(prog, &n);
+    std::vector<char> cubin(n);
+    g_rtc.cubin(prog, cubin.data());
+    g_rtc.destroy(&prog);
+    CUmodule mod = nullptr;
+    if (g_drv.load(&mod, cubin.data()) != CUDA_SUCCESS) return PTAP_ERR_CUDA;
+    if (g_drv.get_fn(&fn, mod, "ptap_jit_numeric") != CUDA_SUCCESS) return PTAP_ERR_CUDA;
+    g_cache[{dev, key}] = fn;
+  }
+  const size_t smem = fast_smem_for(p);
+  if (g_drv.set_attr(fn, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, (int)smem) != CUDA_SUCCESS)
+    return PTAP_ERR_CUDA;
+  int per_sm = 0;
+  if (g_drv.occupancy(&per_sm, fn, p->cfg.block_threads, smem) != CUDA_SUCCESS || per_sm < 1)
+    return PTAP_ERR_CUDA;
+  p->jit_fn = (void*)fn;
+  p->jit_per_sm = per_sm;
+  p->jit_classes = (int)hot.size();
+  p->jit_coverage = total ? (double)covered / (double)total : 0.0;
+  p->jit_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  return PTAP_OK;
+}
+
+int jit_launch(ptap_plan* p, const void* args, int grid, cudaStream_t s) {
+  void* params[1] = {const_cast<void*>(args)};
+  if (g_drv.launch((CUfunction)p->jit_fn, grid, 1, 1, p->cfg.block_threads, 1, 1, (unsigned)p->num_smem,
+                   (CUstream)s, params, nullptr) != CUDA_SUCCESS)
+    return PTAP_ERR_CUDA;
+  return PTAP_OK;
+}
+
+}  // namespace ptap

@@ -54,7 +54,8 @@ class _Config(_c.Structure):
                 ("block_threads", _c.c_int32), ("group_lanes", _c.c_int32),
                 ("ap_slots", _c.c_int32), ("debug_checks", _c.c_int32),
                 ("force_spill", _c.c_int32), ("class_programs", _c.c_int32),
-                ("visit_block_log2", _c.c_int32), ("reserved", _c.c_int32 * 7)]
+                ("visit_block_log2", _c.c_int32), ("specialize", _c.c_int32),
+                ("reserved", _c.c_int32 * 6)]
 
 
 class _Stats(_c.Structure):
@@ -67,7 +68,8 @@ class _Stats(_c.Structure):
                 ("block_threads", _c.c_int32), ("group_lanes", _c.c_int32),
                 ("ap_slots", _c.c_int32), ("kind", _c.c_int32), ("fast_path", _c.c_int32),
                 ("n_classes", _c.c_int32), ("n_segments", _c.c_int32),
-                ("n_pieces", _c.c_int32), ("reserved", _c.c_int32 * 3)]
+                ("n_pieces", _c.c_int32), ("n_specialized", _c.c_int32),
+                ("specialized_permille", _c.c_int32), ("specialize_us", _c.c_int32)]
 
 
 _LIB = None
@@ -199,7 +201,7 @@ class Csr:
 
 def make_config(mode=MODE_OWNER, chunk_entries=0, block_threads=0, group_lanes=0, ap_slots=0,
                 debug_checks=False, force_spill=False, class_programs=True,
-                visit_block_log2=0) -> _Config:
+                visit_block_log2=0, specialize=False) -> _Config:
     cfg = _Config()
     cfg.mode = mode
     cfg.chunk_entries = chunk_entries
@@ -210,6 +212,7 @@ def make_config(mode=MODE_OWNER, chunk_entries=0, block_threads=0, group_lanes=0
     cfg.force_spill = int(bool(force_spill))
     cfg.class_programs = 0 if class_programs else -1
     cfg.visit_block_log2 = visit_block_log2
+    cfg.specialize = 32 if specialize is True else (-1 if not specialize else int(specialize))
     return cfg
 
 

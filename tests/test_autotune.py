@@ -1,0 +1,42 @@
+"""Autotuner: signature and cache logic on the CPU; tuning on the GPU."""
+import numpy as np
+import pytest
+
+from paper_1905_08423_gb300 import autotune
+from paper_1905_08423_gb300 import problems as pb
+
+
+def test_signature_and_cache(tmp_path):
+    A, P = pb.model_problem(9)
+    A2, P2 = pb.algebraic_problem(9, seed=1)
+    s1, s2 = autotune.signature(A, P), autotune.signature(A2, P2)
+    assert s1 == autotune.signature(A, P) and s1 != s2
+    # same sizes, different pattern -> different signature
+    B = pb.CSR(A.nrows, A.ncols, A.row_ptr.copy(), A.col_idx, A.val)
+    B.row_ptr[1] += 0  # unchanged pattern
+    assert autotune.signature(B, P) == s1
+    path = str(tmp_path / "cache.json")
+    assert autotune.load_cache(path) == {}
+    key = autotune.cache_key("GPU", "f32", s1)
+    autotune.save_cache({key: {"config": {"chunk_entries": 4096}, "ms": 1.5}}, path)
+    c = autotune.load_cache(path)
+    assert c[key]["config"] == {"chunk_entries": 4096} and c[key]["ms"] == 1.5
+    open(path, "w").write("not json")
+    assert autotune.load_cache(path) == {}
+
+
+@pytest.mark.gpu
+def test_tune_and_parity(tmp_path):
+    import torch
+    from paper_1905_08423_gb300 import ptap
+    from parity import run_and_check, to_dev
+    A, P = pb.algebraic_problem(14, seed=21)
+    dA, dP = to_dev(A, torch.float64), to_dev(P, torch.float64)
+    path = str(tmp_path / "tune.json")
+    cands = [dict(specialize=False), dict(class_programs=False), dict(mode=ptap.MODE_ATOMIC),
+             dict(chunk_entries=1024, specialize=False)]
+    r = autotune.tune(dA, dP, candidates=cands, reps=2, warmup=1, cache_path=path)
+    assert r.config in cands and r.ms > 0 and len(r.trials) == len(cands) and not r.cached
+    again = autotune.tune(dA, dP, candidates=cands, cache_path=path)
+    assert again.cached and again.config == r.config
+    run_and_check(A, P, torch.float64, ptap.make_config(**r.config))

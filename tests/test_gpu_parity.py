@@ -66,6 +66,7 @@ CONFIGS = [
     dict(chunk_entries=600, block_threads=128),
     dict(visit_block_log2=6),                     # class programs in 64-row blocks
     dict(visit_block_log2=8, chunk_entries=2048),
+    dict(specialize=4, chunk_entries=1024),       # compiled classes and interpreted ones mixed
 ]
 
 
@@ -248,3 +249,18 @@ def test_class_programs_declined():
     P = pb.random_csr(120, 20, 0.1, rng)
     plan, C = run_and_check(A, P, torch.float64)
     assert plan.stats()["fast_path"] == 0
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_specialized_classes(dtype):
+    """Plan-time compiled class code matches the oracle and the interpreter."""
+    for A, P in (pb.model_problem(21), pb.algebraic_problem(15, seed=12), pb.poisson2d_problem(48)):
+        plan, C = run_and_check(A, P, dtype, ptap.make_config(specialize=8))
+        st = plan.stats()
+        assert st["fast_path"] == 1 and 0 < st["n_specialized"] <= 8
+        plan_i, C_i = run_and_check(A, P, dtype, ptap.make_config())
+        assert plan_i.stats()["n_specialized"] == 0
+        tol = 1e-12 if dtype == torch.float64 else 1e-5
+        B = oracle.ptap_bound(rounded(A, dtype), rounded(P, dtype)).val
+        err = np.abs(C.cpu().numpy().astype(np.float64) - C_i.cpu().numpy().astype(np.float64))
+        assert (err <= 2 * tol * B + 1e-300).all()
