@@ -175,6 +175,71 @@ def workload_config(size, n, nnz_a, m, nnz_p, nnz_c, ws):
             "parallelism": f"independent replicas x{ws}" if ws > 1 else "single GPU"}
 
 
+def bench_batch(ptap, pb, dev, tdt, ev, s, count=64, reps=10):
+    """64 uneven triple products (sides U{16..96}; 7-/27-point; trilinear/SA P)."""
+    import torch
+    probs = pb.batch_problems(seed=4, count=count)
+    As, Ps, plans, Cs = [], [], [], []
+    for A, P in probs:
+        dA, dP = ptap.Csr.from_host(A, dev, tdt), ptap.Csr.from_host(P, dev, tdt)
+        plan = ptap.symbolic(dA, dP)
+        As.append(dA)
+        Ps.append(dP)
+        plans.append(plan)
+        Cs.append(torch.empty(plan.nnz, dtype=tdt, device=dev))
+    nnz_c = sum(p.nnz for p in plans)
+    batch = ptap.Batch(plans, As, Ps, Cs)
+    for _ in range(3):
+        batch.numeric()
+        for p, a, q, c in zip(plans, As, Ps, Cs):
+            ptap.numeric(p, a, q, c)
+    torch.cuda.synchronize()
+    a, b, c = ev(), ev(), ev()
+    a.record(s)
+    for _ in range(reps):
+        for p, x, q, y in zip(plans, As, Ps, Cs):
+            ptap.numeric(p, x, q, y)
+    b.record(s)
+    for _ in range(reps):
+        batch.numeric()
+    c.record(s)
+    torch.cuda.synchronize()
+    seq_ms, bat_ms = a.elapsed_time(b) / reps, b.elapsed_time(c) / reps
+    # graph: capture the batch once, rescale A's values in place, replay
+    orig = [x.val.clone() for x in As]
+    gs = torch.cuda.Stream()
+    gs.wait_stream(torch.cuda.current_stream())
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(gs):
+        batch.numeric(stream=gs)
+        gs.synchronize()
+        with torch.cuda.graph(graph, stream=gs):
+            batch.numeric(stream=gs)
+    torch.cuda.current_stream().wait_stream(gs)
+    replay_ms = []
+    for r in range(reps):
+        g = torch.Generator(device=dev).manual_seed(40 + r)
+        for x, o in zip(As, orig):
+            x.val.copy_(o * (0.5 + 1.5 * torch.rand(o.shape, generator=g, device=dev, dtype=o.dtype)))
+        e0, e1 = ev(), ev()
+        e0.record(s)
+        graph.replay()
+        e1.record(s)
+        torch.cuda.synchronize()
+        replay_ms.append(e0.elapsed_time(e1))
+    for p in plans:
+        p.check()
+        p.destroy()
+    batch.destroy()
+    return {"problems": count, "nnz_c_total": nnz_c,
+            "rows_total": int(sum(A.nrows for A, _ in probs)),
+            "batched": {"ms": round(bat_ms, 4), "c_nnz_per_s": round(nnz_c / (bat_ms * 1e-3), 1)},
+            "sequential": {"ms": round(seq_ms, 4), "c_nnz_per_s": round(nnz_c / (seq_ms * 1e-3), 1)},
+            "speedup": round(seq_ms / bat_ms, 3),
+            "graph_replay_ms_median": round(statistics.median(replay_ms), 4),
+            "graph_replays": reps, "rescale": "A values x U(0.5, 2) per entry between replays"}
+
+
 def dist_setup():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -253,6 +318,7 @@ def main():
     ap.add_argument("--mode", default="owner", choices=["owner", "atomic"])
     ap.add_argument("--no-extras", action="store_true", help="numeric only (no comparator etc.)")
     ap.add_argument("--no-tune", action="store_true", help="default launch parameters, no autotuning")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 64-problem batch")
     ap.add_argument("--config", default=None,
                     help="launch parameters as JSON (ptap.make_config keywords); skips autotuning")
     args = ap.parse_args()
@@ -504,6 +570,11 @@ def main():
             plan64.destroy()
             del d64A, d64P, C64
             torch.cuda.empty_cache()
+
+        # ---- uneven batch: 64 products in one persistent launch vs 64 launches, then
+        #      numeric-only re-products replayed from a CUDA graph after rescaling A
+        if not args.no_batch:
+            out["batch"] = bench_batch(ptap, pb, dev, tdt, ev, s)
 
         # ---- CPU baseline: the oracle on the host cores (rank 0 only)
         if rank == 0:

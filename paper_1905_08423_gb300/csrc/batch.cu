@@ -13,6 +13,7 @@
 #include <new>
 #include <numeric>
 
+#include "fastkern.cuh"
 #include "owner.cuh"
 
 namespace ptap {
@@ -40,13 +41,61 @@ __global__ void __launch_bounds__(256) k_batch_owner(const NumArgs<V>* __restric
   }
 }
 
+// Fast variant: every plan of the batch runs class programs (interpreted).
+struct NoSpecial {
+  template <typename V>
+  __device__ bool operator()(const ptapk::FastArgs<V>&, int32_t, int32_t, int32_t, int32_t, int32_t, V*,
+                             const int32_t*) const {
+    return false;
+  }
+};
+
+template <typename V>
+__global__ void __launch_bounds__(256) k_batch_fast(const ptapk::FastArgs<V>* __restrict__ probs,
+                                                   const int32_t* __restrict__ items, int32_t nitems,
+                                                   int32_t* counter, int CH, int maxr, int max_rows,
+                                                   int prog_cap) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ int32_t item;
+  ptapk::FastSmem<V> sm(smraw, CH, maxr, max_rows, prog_cap);
+  for (;;) {
+    if (threadIdx.x == 0) item = atomicAdd(counter, 1);
+    __syncthreads();
+    const int32_t it = item;
+    __syncthreads();
+    if (it >= nitems) break;
+    const ptapk::FastArgs<V> a = probs[items[2 * it]];
+    ptapk::fast_chunk<V>(a, items[2 * it + 1], sm, NoSpecial());
+  }
+}
+
 template <typename V>
 static int batch_create_t(ptap_batch* b, ptap_plan* const* plans, const ptap_csr* A,
                           const ptap_csr* P, void* const* C, cudaStream_t s) {
   std::vector<NumArgs<V>> h(b->count);
+  std::vector<ptapk::FastArgs<V>> hf(b->count);
   std::vector<std::pair<int64_t, std::pair<int32_t, int32_t>>> work;
   for (int32_t q = 0; q < b->count; ++q) {
     ptap_plan* p = plans[q];
+    if (b->fast) {
+      ptapk::FastArgs<V>& f = hf[q];
+      f.A = ptapk::FCsr<V>{A[q].nrows, A[q].ncols, A[q].row_ptr, A[q].col_idx, (const V*)A[q].val};
+      f.P = ptapk::FCsr<V>{P[q].nrows, P[q].ncols, P[q].row_ptr, P[q].col_idx, (const V*)P[q].val};
+      f.c_rp = p->c_rp;
+      f.c_val = (V*)C[q];
+      f.chunk_row = p->chunk_row;
+      f.chunk_piece = p->chunk_piece;
+      f.piece_f0 = p->piece_f0;
+      f.piece_meta = p->piece_meta;
+      f.frows = p->chunk_frows;
+      f.pool = p->class_pool;
+      f.class_off = p->class_off;
+      f.nchunks = p->nchunks;
+      f.CH = p->cfg.chunk_entries;
+      f.max_rows = std::max(p->max_chunk_rows, 1);
+      f.prog_cap = (p->class_maxlen + 15) & ~15;
+      f.maxr = std::max(p->class_maxr, 1);
+    }
     NumArgs<V>& a = h[q];
     a.A = CsrV<V>{A[q].nrows, A[q].ncols, A[q].row_ptr, A[q].col_idx, (const V*)A[q].val};
     a.P = CsrV<V>{P[q].nrows, P[q].ncols, P[q].row_ptr, P[q].col_idx, (const V*)P[q].val};
@@ -75,12 +124,39 @@ static int batch_create_t(ptap_batch* b, ptap_plan* const* plans, const ptap_csr
     items[2 * t + 1] = work[t].second.second;
   }
   b->total_items = (int64_t)work.size();
-  PTAP_TRY(b->mem.get(&b->d_desc, h.size() * sizeof(NumArgs<V>)));
+  const size_t dbytes = b->fast ? hf.size() * sizeof(ptapk::FastArgs<V>) : h.size() * sizeof(NumArgs<V>);
+  PTAP_TRY(b->mem.get(&b->d_desc, dbytes));
   PTAP_TRY(b->mem.get_n(&b->d_items, (int64_t)items.size()));
-  PTAP_CUDA(cudaMemcpyAsync(b->d_desc, h.data(), h.size() * sizeof(NumArgs<V>), cudaMemcpyHostToDevice, s));
+  if (b->fast)
+    PTAP_CUDA(cudaMemcpyAsync(b->d_desc, hf.data(), dbytes, cudaMemcpyHostToDevice, s));
+  else
+    PTAP_CUDA(cudaMemcpyAsync(b->d_desc, h.data(), dbytes, cudaMemcpyHostToDevice, s));
   PTAP_CUDA(cudaMemcpyAsync(b->d_items, items.data(), items.size() * sizeof(int32_t),
                             cudaMemcpyHostToDevice, s));
   PTAP_CUDA(cudaStreamSynchronize(s));
+  return PTAP_OK;
+}
+
+template <typename V>
+static int batch_prepare_fast(ptap_batch* b) {
+  const size_t smem = ptapk::fast_smem_bytes<V>(b->fast_ch, b->cfg.block_threads, b->fast_maxr,
+                                                b->max_chunk_rows, b->fast_prog_cap);
+  PTAP_CUDA(cudaFuncSetAttribute(k_batch_fast<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 0;
+  PTAP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_fast<V>, b->cfg.block_threads, smem));
+  if (per_sm < 1) return PTAP_ERR_INVALID;
+  b->smem = smem;
+  b->grid = (int)std::max<int64_t>(1, std::min<int64_t>(b->total_items, (int64_t)num_sms() * per_sm));
+  return PTAP_OK;
+}
+
+template <typename V>
+static int batch_launch_fast(ptap_batch* b, cudaStream_t s) {
+  PTAP_CUDA(cudaMemsetAsync(b->d_counter, 0, sizeof(int32_t), s));
+  k_batch_fast<V><<<b->grid, b->cfg.block_threads, b->smem, s>>>(
+      (const ptapk::FastArgs<V>*)b->d_desc, b->d_items, (int32_t)b->total_items, b->d_counter, b->fast_ch,
+      b->fast_maxr, b->max_chunk_rows, b->fast_prog_cap);
+  PTAP_LAUNCHED();
   return PTAP_OK;
 }
 
@@ -131,9 +207,13 @@ static int batch_launch_g(ptap_batch* b, cudaStream_t s) {
     return PTAP_ERR_INVALID;                                       \
   } while (0)
 
-static int batch_prepare(ptap_batch* b) { PTAP_BATCH_DISPATCH(b, (batch_prepare_g<V, G>(b))); }
+static int batch_prepare(ptap_batch* b) {
+  if (b->fast) return b->dtype == PTAP_F64 ? batch_prepare_fast<double>(b) : batch_prepare_fast<float>(b);
+  PTAP_BATCH_DISPATCH(b, (batch_prepare_g<V, G>(b)));
+}
 
 static int batch_launch(ptap_batch* b, cudaStream_t s) {
+  if (b->fast) return b->dtype == PTAP_F64 ? batch_launch_fast<double>(b, s) : batch_launch_fast<float>(b, s);
   PTAP_BATCH_DISPATCH(b, (batch_launch_g<V, G>(b, s)));
 }
 
@@ -148,14 +228,26 @@ extern "C" int ptap_batch_create(ptap_plan* const* plans, const ptap_csr* A, con
   *out = nullptr;
   const ptap_plan* p0 = plans[0];
   if (!p0) return PTAP_ERR_INVALID;
-  int32_t max_rows = 1;
+  int32_t max_rows = 1, fast_ch = 1, fast_maxr = 1, fast_prog_cap = 16;
+  bool all_fast = true;
   for (int32_t q = 0; q < count; ++q) {
     const ptap_plan* p = plans[q];
     if (!p || p->kind != 0 || p->dtype != p0->dtype) return PTAP_ERR_INVALID;
+    all_fast = all_fast && p->fast && p->cfg.mode == PTAP_MODE_OWNER &&
+               p->cfg.block_threads == p0->cfg.block_threads;
+    fast_ch = std::max(fast_ch, p->cfg.chunk_entries);
+    fast_maxr = std::max(fast_maxr, p->class_maxr);
+    fast_prog_cap = std::max(fast_prog_cap, (p->class_maxlen + 15) & ~15);
+  }
+  for (int32_t q = 0; q < count && !all_fast; ++q) {
+    const ptap_plan* p = plans[q];
     if (p->cfg.chunk_entries != p0->cfg.chunk_entries || p->cfg.group_lanes != p0->cfg.group_lanes ||
         p->cfg.ap_slots != p0->cfg.ap_slots || p->cfg.block_threads != p0->cfg.block_threads ||
         p->cfg.force_spill != p0->cfg.force_spill)
       return PTAP_ERR_INVALID;
+  }
+  for (int32_t q = 0; q < count; ++q) {
+    const ptap_plan* p = plans[q];
     PTAP_TRY(ptap::check_numeric_inputs(p, &A[q], &P[q]));
     if (p->nnz_c > 0 && !C_vals[q]) return PTAP_ERR_INVALID;
     max_rows = std::max(max_rows, p->max_chunk_rows);
@@ -168,6 +260,10 @@ extern "C" int ptap_batch_create(ptap_plan* const* plans, const ptap_csr* A, con
   b->count = count;
   b->cfg = p0->cfg;
   b->max_chunk_rows = max_rows;
+  b->fast = all_fast;
+  b->fast_ch = fast_ch;
+  b->fast_maxr = fast_maxr;
+  b->fast_prog_cap = fast_prog_cap;
   int rc = b->mem.get_n(&b->d_counter, 1);
   if (rc == PTAP_OK) rc = b->mem.get_n(&b->status, 1);
   if (rc == PTAP_OK && cudaMemsetAsync(b->status, 0, sizeof(int32_t), s) != cudaSuccess) rc = PTAP_ERR_CUDA;

@@ -221,6 +221,8 @@ struct ptap_batch {
   ptap::Config cfg;
   size_t smem = 0;  // launch configuration, settled at creation
   int grid = 0;
+  bool fast = false;  // every plan runs class programs: the fast batch kernel
+  int fast_ch = 0, fast_maxr = 0, fast_prog_cap = 0;
 };
 
 namespace ptap {

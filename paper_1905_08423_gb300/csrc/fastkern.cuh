@@ -143,45 +143,65 @@ __host__ __device__ inline size_t fast_smem_bytes(int CH, int threads, int maxr,
          (size_t)(threads / 32) * prog_cap;
 }
 
-// The kernel body.  `special(a, cls, f, f1, i0, i1, acc, roff)` runs a piece
-// of a class it has straight-line code for and returns true; otherwise the
-// interpreter runs it from the class's program.
+// Per-warp pointers into the shared-memory carve-up (dims are the largest
+// over the problems a kernel serves: one product, or a batch).
+template <typename V>
+struct FastSmem {
+  V* acc;
+  V* Rs;
+  int32_t* roff;
+  uint8_t* prog;
+  __device__ FastSmem(unsigned char* raw, int CH, int maxr, int max_rows, int prog_cap) {
+    const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int CHa = (CH + 3) & ~3;
+    acc = (V*)raw;
+    Rs = acc + CHa + (size_t)warp * 32 * maxr;
+    roff = (int32_t*)(acc + CHa + (size_t)nwarps * 32 * maxr);
+    prog = (uint8_t*)(roff + ((max_rows + 1 + 3) & ~3)) + warp * prog_cap;
+  }
+};
+
+// One chunk c of a product.  `special(a, cls, f, f1, i0, i1, acc, roff)` runs
+// a piece of a class it has straight-line code for and returns true;
+// otherwise the interpreter runs it from the class's program.
+template <typename V, typename Special>
+__device__ __forceinline__ void fast_chunk(const FastArgs<V>& a, int32_t c, FastSmem<V>& sm,
+                                           Special special) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+  V* acc = sm.acc;
+  int32_t* roff = sm.roff;
+  const int32_t i0 = a.chunk_row[c], i1 = a.chunk_row[c + 1];
+  const int32_t base = a.c_rp[i0], nnz = a.c_rp[i1] - base;
+  for (int t = threadIdx.x; t < nnz; t += blockDim.x) acc[t] = V(0);
+  for (int t = threadIdx.x; t <= i1 - i0; t += blockDim.x) roff[t] = a.c_rp[i0 + t] - base;
+  __syncthreads();
+  // the chunk's pieces (<= 32 rows of one class) go round-robin to the warps
+  int32_t loaded = -1;
+  const int32_t pe = a.chunk_piece[c + 1];
+  for (int32_t pc = a.chunk_piece[c] + warp; pc < pe; pc += nwarps) {
+    const int32_t meta = a.piece_meta[pc], f0 = a.piece_f0[pc];
+    const int32_t cls = meta >> 6, f1 = f0 + (meta & 63);
+    if (special(a, cls, f0, f1, i0, i1, acc, roff)) continue;
+    if (cls != loaded) {
+      __syncwarp();
+      const uint8_t* src = a.pool + a.class_off[cls];
+      for (int x = lane; x < a.prog_cap; x += 32) sm.prog[x] = src[x];
+      __syncwarp();
+      loaded = cls;
+    }
+    fast_piece<V>(a, sm.prog, sm.Rs, f0, f1, i0, i1, acc, roff);
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < nnz; t += blockDim.x) a.c_val[base + t] = acc[t];
+  __syncthreads();
+}
+
+// The single-product kernel body: chunks strided over the grid.
 template <typename V, typename Special>
 __device__ __forceinline__ void fast_kernel_body(const FastArgs<V>& a, Special special) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
-  const int CHa = (a.CH + 3) & ~3;
-  V* acc = (V*)smraw;
-  V* Rs = acc + CHa + (size_t)warp * 32 * a.maxr;
-  int32_t* roff = (int32_t*)(acc + CHa + (size_t)nwarps * 32 * a.maxr);
-  uint8_t* progs = (uint8_t*)(roff + ((a.max_rows + 1 + 3) & ~3));
-  uint8_t* prog = progs + warp * a.prog_cap;
-  for (int32_t c = blockIdx.x; c < a.nchunks; c += gridDim.x) {
-    const int32_t i0 = a.chunk_row[c], i1 = a.chunk_row[c + 1];
-    const int32_t base = a.c_rp[i0], nnz = a.c_rp[i1] - base;
-    for (int t = threadIdx.x; t < nnz; t += blockDim.x) acc[t] = V(0);
-    for (int t = threadIdx.x; t <= i1 - i0; t += blockDim.x) roff[t] = a.c_rp[i0 + t] - base;
-    __syncthreads();
-    // the chunk's pieces (<= 32 rows of one class) go round-robin to the warps
-    int32_t loaded = -1;
-    const int32_t pe = a.chunk_piece[c + 1];
-    for (int32_t pc = a.chunk_piece[c] + warp; pc < pe; pc += nwarps) {
-      const int32_t meta = a.piece_meta[pc], f0 = a.piece_f0[pc];
-      const int32_t cls = meta >> 6, f1 = f0 + (meta & 63);
-      if (special(a, cls, f0, f1, i0, i1, acc, roff)) continue;
-      if (cls != loaded) {
-        __syncwarp();
-        const uint8_t* src = a.pool + a.class_off[cls];
-        for (int x = lane; x < a.prog_cap; x += 32) prog[x] = src[x];
-        __syncwarp();
-        loaded = cls;
-      }
-      fast_piece<V>(a, prog, Rs, f0, f1, i0, i1, acc, roff);
-    }
-    __syncthreads();
-    for (int t = threadIdx.x; t < nnz; t += blockDim.x) a.c_val[base + t] = acc[t];
-    __syncthreads();
-  }
+  FastSmem<V> sm(smraw, a.CH, a.maxr, a.max_rows, a.prog_cap);
+  for (int32_t c = blockIdx.x; c < a.nchunks; c += gridDim.x) fast_chunk<V>(a, c, sm, special);
 }
 
 }  // namespace ptapk
