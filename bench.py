@@ -541,7 +541,7 @@ def main():
         if args.dtype == "f32":
             d64A = ptap.Csr.from_host(A, dev, torch.float64)
             d64P = ptap.Csr.from_host(P, dev, torch.float64)
-            cands = [dict(), dict(specialize=True), dict(chunk_entries=16384, specialize=True)]
+            cands = [dict(), dict(specialize=4), dict(specialize=8), dict(chunk_entries=16384, specialize=8)]
             t64 = autotune.tune(d64A, d64P, candidates=cands, reps=3, warmup=2, cache_path=None,
                                 use_cache=False) if tuned else None
             plan64 = ptap.symbolic(d64A, d64P, ptap.make_config(**(t64.config if t64 else {})))

@@ -25,8 +25,10 @@ DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "ptap_autotune.j
 # Candidate configurations (keyword arguments of ptap.make_config).
 CANDIDATES = [
     dict(),
-    dict(specialize=True),
-    dict(chunk_entries=16384, specialize=True),
+    dict(specialize=8),
+    dict(specialize=4),
+    dict(specialize=16),
+    dict(chunk_entries=16384, specialize=8),
     dict(chunk_entries=4096),
     dict(visit_block_log2=8),
     dict(class_programs=False),

@@ -130,7 +130,7 @@ struct Config {
   int class_programs = 1;     // fast path by fine-row classes where the patterns allow
   int visit_block_log2 = 0;   // fast path visit order: blocks of 2^b fine rows (0 = class-major)
   int jit = 0;                // specialise the most frequent classes with NVRTC
-  int jit_max_classes = 32;
+  int jit_max_classes = 8;
   int block_threads = 256;
   int group_lanes = 8;
   int ap_slots = 64;

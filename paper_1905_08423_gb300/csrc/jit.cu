@@ -4,8 +4,9 @@
 // goes to which slot of the row of A P, and where each outer-product term
 // lands in C) at run time.  For the classes that carry most of a plan's fine
 // rows this file writes the same computation as straight-line CUDA -- slots
-// become registers, positions become immediate offsets, and each coarse row
-// of P(I,:) gets one guarded block of accumulations -- compiles it for sm_103a
+// become registers, the products become immediate offsets, and the outer
+// product becomes a short loop over P(I,:) whose offsets come from a constant
+// table -- compiles it for sm_103a
 // with NVRTC together with fastkern.cuh, and loads it.  Other classes still
 // run on the interpreter inside the same kernel.  Nothing here changes what is
 // computed: the generated code performs the products of the program in the
@@ -20,6 +21,7 @@
 #include <nvrtc.h>
 
 #include <algorithm>
+#include <cstdarg>
 #include <chrono>
 #include <map>
 #include <mutex>
@@ -104,54 +106,69 @@ uint64_t fnv64(const std::string& s) {
   return h;
 }
 
-// Straight-line code for one class program g (layout in fastkern.cuh).
+// printf-style append that never truncates.
+void appendf(std::string& o, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  const int n = vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (n < 0) return;
+  if (n < (int)sizeof buf) {
+    o += buf;
+    return;
+  }
+  std::string big((size_t)n + 1, '\0');
+  va_start(ap, fmt);
+  vsnprintf(&big[0], big.size(), fmt, ap);
+  va_end(ap);
+  big.resize((size_t)n);
+  o += big;
+}
+
+// Code for one class program g (layout in fastkern.cuh).  The row of A P is
+// straight-line code with its r slots in registers (Alg. 3); the outer
+// product is a loop over the pI entries of P(I,:) whose body adds the r slots
+// at offsets sigma(s, t) read from a per-class constant table (Alg. 8).  The
+// loop keeps the code of a class near r accumulations instead of r * pI: the
+// instruction cache, not the issue rate, limits how many classes pay off.
 std::string gen_class(int cls, const uint8_t* g) {
   const int na = g[0], r = g[1], pI = g[2];
   const uint8_t* pa = g + 8;
   const uint8_t* tsec = g + 8 + ((na + 7) & ~7);
   const uint8_t* ssec = tsec + 8 * na;
   std::string o;
-  char buf[256];
-  snprintf(buf, sizeof buf,
-           "__device__ __forceinline__ void cls_%d(const FastArgs<V>& a, int32_t f, int32_t f1, int32_t i0,"
-           " int32_t i1, V* acc, const int32_t* roff) {\n",
-           cls);
-  o += buf;
+  appendf(o, "static __constant__ unsigned char sg_%d[%d] = {", cls, pI * r);
+  for (int s = 0; s < pI; ++s)
+    for (int t = 0; t < r; ++t) appendf(o, "%d,", (int)ssec[t * 8 + s]);
+  o += "};\n";
+  appendf(o,
+          "__device__ __forceinline__ void cls_%d(const FastArgs<V>& a, int32_t f, int32_t f1, int32_t i0,"
+          " int32_t i1, V* acc, const int32_t* roff) {\n",
+          cls);
   o += "  const int lane = threadIdx.x & 31;\n  const bool valid = f + lane < f1;\n"
        "  const int32_t I = a.frows[valid ? f + lane : f];\n  const int32_t ra = a.A.rp[I];\n"
        "  const int32_t* Aci = a.A.ci + ra;\n  const V* Av = a.A.val + ra;\n  const V* Pv = a.P.val;\n";
-  for (int x = 0; x < na; ++x) {
-    snprintf(buf, sizeof buf, "  const V a%d = Av[%d];\n  const int32_t q%d = a.P.rp[Aci[%d]];\n", x, x, x, x);
-    o += buf;
-  }
+  for (int x = 0; x < na; ++x)
+    appendf(o, "  const V a%d = Av[%d];\n  const int32_t q%d = a.P.rp[Aci[%d]];\n", x, x, x, x);
   // slots of the row of A P, products summed in the interpreter's (a, b) order
   for (int t = 0; t < r; ++t) {
-    bool first = true;
-    snprintf(buf, sizeof buf, "  V R%d = V(0);\n", t);
-    o += buf;
+    appendf(o, "  V R%d = V(0);\n", t);
     for (int x = 0; x < na; ++x)
       for (int b = 0; b < pa[x]; ++b)
-        if (tsec[x * 8 + b] == t) {
-          snprintf(buf, sizeof buf, "  R%d += a%d * Pv[q%d + %d];\n", t, x, x, b);
-          o += buf;
-          first = false;
-        }
-    (void)first;
+        if (tsec[x * 8 + b] == t) appendf(o, "  R%d += a%d * Pv[q%d + %d];\n", t, x, x, b);
   }
-  o += "  const int32_t rp = a.P.rp[I];\n";
-  for (int s = 0; s < pI; ++s) {
-    snprintf(buf, sizeof buf,
-             "  { const int32_t i = a.P.ci[rp + %d]; const V w = a.P.val[rp + %d];\n"
-             "    if (valid && i >= i0 && i < i1) { V* c = acc + roff[i - i0];\n",
-             s, s);
-    o += buf;
-    for (int t = 0; t < r; ++t) {
-      snprintf(buf, sizeof buf, "      atomicAdd(c + %d, w * R%d);\n", (int)ssec[t * 8 + s], t);
-      o += buf;
-    }
-    o += "    } }\n";
-  }
-  o += "}\n";
+  // outer product: the next entry of P(I,:) is loaded while this one is added
+  o += "  const int32_t rp = a.P.rp[I];\n  int32_t in = a.P.ci[rp];\n  V wn = a.P.val[rp];\n";
+  appendf(o,
+          "#pragma unroll 1\n  for (int s = 0; s < %d; ++s) {\n"
+          "    const int32_t i = in;\n    const V w = wn;\n"
+          "    if (s + 1 < %d) {\n      in = a.P.ci[rp + s + 1];\n      wn = a.P.val[rp + s + 1];\n    }\n"
+          "    if (valid && i >= i0 && i < i1) {\n      V* c = acc + roff[i - i0];\n"
+          "      const unsigned char* sg = sg_%d + s * %d;\n",
+          pI, pI, cls, r);
+  for (int t = 0; t < r; ++t) appendf(o, "      atomicAdd(c + sg[%d], w * R%d);\n", t, t);
+  o += "    }\n  }\n}\n";
   return o;
 }
 
@@ -204,7 +221,7 @@ int jit_prepare(ptap_plan* p) {
     src += buf;
   }
   src += "      default: return false;\n    }\n  }\n};\n"
-         "extern \"C\" __global__ void __launch_bounds__(256) ptap_jit_numeric(FastArgs<V> a) {\n"
+         "extern \"C\" __global__ void __launch_bounds__(256, 4) ptap_jit_numeric(FastArgs<V> a) {\n"
          "  fast_kernel_body<V>(a, Special());\n}\n";
   int dev = 0;
   PTAP_CUDA(cudaGetDevice(&dev));

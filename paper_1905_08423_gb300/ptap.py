@@ -212,7 +212,7 @@ def make_config(mode=MODE_OWNER, chunk_entries=0, block_threads=0, group_lanes=0
     cfg.force_spill = int(bool(force_spill))
     cfg.class_programs = 0 if class_programs else -1
     cfg.visit_block_log2 = visit_block_log2
-    cfg.specialize = 32 if specialize is True else (-1 if not specialize else int(specialize))
+    cfg.specialize = 8 if specialize is True else (-1 if not specialize else int(specialize))
     return cfg
 
 
