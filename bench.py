@@ -175,10 +175,11 @@ def workload_config(size, n, nnz_a, m, nnz_p, nnz_c, ws):
             "parallelism": f"independent replicas x{ws}" if ws > 1 else "single GPU"}
 
 
-def bench_batch(ptap, pb, dev, tdt, ev, s, count=64, reps=10):
+def bench_batch(ptap, pb, dev, tdt, ev, s, count=64, reps=10, probs=None):
     """64 uneven triple products (sides U{16..96}; 7-/27-point; trilinear/SA P)."""
     import torch
-    probs = pb.batch_problems(seed=4, count=count)
+    if probs is None:
+        probs = pb.batch_problems(seed=4, count=count)
     As, Ps, plans, Cs = [], [], [], []
     for A, P in probs:
         dA, dP = ptap.Csr.from_host(A, dev, tdt), ptap.Csr.from_host(P, dev, tdt)
@@ -238,6 +239,145 @@ def bench_batch(ptap, pb, dev, tdt, ev, s, count=64, reps=10):
             "speedup": round(seq_ms / bat_ms, 3),
             "graph_replay_ms_median": round(statistics.median(replay_ms), 4),
             "graph_replays": reps, "rescale": "A values x U(0.5, 2) per entry between replays"}
+
+
+def bench_algebraic(ptap, autotune, pb, dev, ev, s, steps, tuned_ok=True):
+    """The irregular algebraic case: 27-point lognormal operator on 200^3, SA 3^3 P, FP64."""
+    import torch
+    A, P = pb.algebraic_problem(200, seed=3)
+    dA = ptap.Csr.from_host(A, dev, torch.float64)
+    dP = ptap.Csr.from_host(P, dev, torch.float64)
+    cands = [dict(), dict(specialize=4), dict(specialize=8), dict(class_programs=False)]
+    t = (autotune.tune(dA, dP, candidates=cands, reps=3, warmup=2, cache_path=None, use_cache=False)
+         if tuned_ok else None)
+    cfg_kw = t.config if t else {}
+    e0, e1 = ev(), ev()
+    e0.record(s)
+    plan = ptap.symbolic(dA, dP, ptap.make_config(**cfg_kw))
+    e1.record(s)
+    torch.cuda.synchronize()
+    st = plan.stats()
+    C = torch.empty(plan.nnz, dtype=torch.float64, device=dev)
+    for _ in range(3):
+        ptap.numeric(plan, dA, dP, C)
+    k = max(5, steps // 10)
+    a, b = ev(), ev()
+    a.record(s)
+    for _ in range(k):
+        ptap.numeric(plan, dA, dP, C)
+    b.record(s)
+    torch.cuda.synchronize()
+    plan.check()
+    ms = a.elapsed_time(b) / k
+    by = alg_bytes(A.nrows, A.nnz, P.ncols, P.nnz, plan.nnz, 8)
+    peak = max(st["symbolic_peak_bytes"], st["plan_bytes"] + plan.nnz * 8)
+    # the two-step comparator on the same input
+    plan2 = ptap.two_step_symbolic(dA, dP)
+    st2 = plan2.stats()
+    C2 = torch.empty(plan2.nnz, dtype=torch.float64, device=dev)
+    for _ in range(2):
+        ptap.numeric(plan2, dA, dP, C2)
+    a2, b2 = ev(), ev()
+    a2.record(s)
+    for _ in range(3):
+        ptap.numeric(plan2, dA, dP, C2)
+    b2.record(s)
+    torch.cuda.synchronize()
+    two_ms = a2.elapsed_time(b2) / 3
+    two_peak = max(st2["symbolic_peak_bytes"], st2["plan_bytes"] + plan2.nnz * 8)
+    # norm-wise: entries that cancel to rounding level differ relatively
+    same = bool((C - C2).abs().max() <= 1e-10 * C.abs().max())
+    hbm_peak, _ = peaks()
+    out = {"workload": "27-point lognormal(0,1) operator on 200^3 (8,000,000 rows), SA 3^3 P, FP64",
+           "nnz_a": int(A.nnz), "m": int(P.ncols), "nnz_p": int(P.nnz), "nnz_c": int(plan.nnz),
+           "ms_per_step": round(ms, 4), "value": round(by / (ms * 1e-3) / 1e9, 2), "unit": "GB/s",
+           "hbm_frac": round(by / (ms * 1e-3) / 1e9 / hbm_peak, 4),
+           "c_nnz_per_s": round(plan.nnz / (ms * 1e-3), 1),
+           "symbolic_ms": round(e0.elapsed_time(e1), 2),
+           "launch_config": cfg_kw, "fast_path": st["fast_path"], "classes": st["n_classes"],
+           "specialized_classes": st["n_specialized"],
+           "two_step": {"ms_per_step": round(two_ms, 4), "speedup_all_at_once": round(two_ms / ms, 3),
+                        "agrees_with_all_at_once": same},
+           "peak_mb": {"all_at_once": round(peak / 2**20, 1), "two_step": round(two_peak / 2**20, 1),
+                       "ratio": round(peak / two_peak, 4)}}
+    plan2.destroy()
+    plan.destroy()
+    del C, C2, dA, dP
+    torch.cuda.empty_cache()
+    return out
+
+
+def bench_gd(ptap, pb, dev, ev, s, size=512, steps=200):
+    """Gradient descent on P's values through the coarse operator (2D Poisson, SA 2x2 P).
+
+    Loss ||P^T A P - C_target||_F^2 on C's pattern; C_target is the product with
+    P's values perturbed by N(0, 0.05) noise.  The step size is fixed once: the
+    largest of 1, 1/2, 1/4, ... whose first step lowers the loss.
+    """
+    import torch
+    A, P = pb.poisson2d_problem(size)
+    Pt = pb.perturb_values(P, seed=5)
+    out = {"workload": f"2D 5-point Poisson {size}^2, SA 2x2 P, loss ||P^T A P - C_target||_F^2",
+           "steps": steps}
+    for tdt, name in ((torch.float32, "f32"), (torch.float64, "f64")):
+        dA = ptap.Csr.from_host(A, dev, tdt)
+        dP = ptap.Csr.from_host(P, dev, tdt)
+        plan = ptap.symbolic(dA, dP)
+        Ct = ptap.numeric(plan, dA, ptap.Csr.from_host(Pt, dev, tdt))
+        Av = dA.val
+        Pv = dP.val.clone().requires_grad_(True)
+
+        def loss_and_grad():
+            Pv.grad = None
+            C = ptap.PtAP.apply(Av, Pv, plan, dA, dP)
+            loss = ((C - Ct) ** 2).sum()
+            loss.backward()
+            return loss.detach()
+
+        L0 = loss_and_grad()
+        g0 = Pv.grad.clone()
+        lr = 1.0
+        with torch.no_grad():
+            for _ in range(40):
+                trial = ((ptap.PtAP.apply(Av, Pv - lr * g0, plan, dA, dP) - Ct) ** 2).sum()
+                if trial < L0:
+                    break
+                lr *= 0.5
+        # forward and backward alone (ms per call), then the descent from the start
+        p0 = Pv.detach().clone()
+        for _ in range(3):
+            loss_and_grad()
+        f0, f1, f2 = ev(), ev(), ev()
+        f0.record(s)
+        for _ in range(20):
+            with torch.no_grad():
+                ptap.PtAP.apply(Av, Pv, plan, dA, dP)
+        f1.record(s)
+        for _ in range(20):
+            loss_and_grad()
+        f2.record(s)
+        torch.cuda.synchronize()
+        with torch.no_grad():
+            Pv.copy_(p0)
+        # the losses stay in the compute dtype: a cross-dtype item store is a host round trip
+        losses = torch.empty(steps, dtype=tdt, device=dev)
+        torch.cuda.synchronize()
+        a, b = ev(), ev()
+        a.record(s)
+        for k in range(steps):
+            losses[k].copy_(loss_and_grad())
+            with torch.no_grad():
+                Pv.sub_(Pv.grad, alpha=lr)
+        b.record(s)
+        torch.cuda.synchronize()
+        h = losses.cpu().tolist()
+        out[name] = {"lr": lr, "loss": {str(i): h[i] for i in (0, 1, 10, 50, 100, steps - 1) if i < steps},
+                     "monotone": all(y <= x for x, y in zip(h, h[1:])),
+                     "ms_per_step": round(a.elapsed_time(b) / steps, 4),
+                     "forward_ms": round(f0.elapsed_time(f1) / 20, 4),
+                     "loss_and_grad_ms": round(f1.elapsed_time(f2) / 20, 4)}
+        plan.destroy()
+    return out
 
 
 def dist_setup():
@@ -571,10 +711,22 @@ def main():
             del d64A, d64P, C64
             torch.cuda.empty_cache()
 
+        # ---- the irregular algebraic case (27-point lognormal, SA P), FP64
+        out["algebraic"] = bench_algebraic(ptap, autotune, pb, dev, ev, s, args.steps, tuned is not None)
+
+        # ---- gradient descent on P through the coarse operator, FP32 and FP64
+        out["gd"] = bench_gd(ptap, pb, dev, ev, s)
+
         # ---- uneven batch: 64 products in one persistent launch vs 64 launches, then
         #      numeric-only re-products replayed from a CUDA graph after rescaling A
         if not args.no_batch:
-            out["batch"] = bench_batch(ptap, pb, dev, tdt, ev, s)
+            probs = pb.batch_problems(seed=4, count=64)
+            out["batch"] = bench_batch(ptap, pb, dev, tdt, ev, s, probs=probs)
+            other = torch.float64 if tdt == torch.float32 else torch.float32
+            out["batch"]["dtype"] = args.dtype
+            out["batch_" + ("f64" if other == torch.float64 else "f32")] = bench_batch(
+                ptap, pb, dev, other, ev, s, probs=probs)
+            del probs
 
         # ---- CPU baseline: the oracle on the host cores (rank 0 only)
         if rank == 0:

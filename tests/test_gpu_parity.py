@@ -192,6 +192,51 @@ def test_autograd_function():
     assert abs(fd - an) <= 1e-6 * abs(an)
 
 
+def _oracle_gd(A, P, Pt, lr, steps):
+    """Gradient descent on P's values with the oracle's product and gradient."""
+    Ct = oracle.ptap(A, Pt)
+    pv, hist = P.val.copy(), []
+    for _ in range(steps):
+        Pc = P.with_values(pv)
+        C = oracle.ptap(A, Pc)
+        d = C.val - Ct.val
+        hist.append(float((d * d).sum()))
+        _, gP = oracle.ptap_backward(A, Pc, pb.CSR(C.nrows, C.ncols, C.row_ptr, C.col_idx, 2 * d))
+        pv = pv - lr * gP
+    return hist
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_gradient_descent_on_P(dtype):
+    """Descent on P's values through the coarse operator follows the oracle's descent.
+
+    Loss ||P^T A P - C_target||_F^2, C_target from P's values plus N(0, 0.05)
+    noise; fixed step 1/32 (the largest power of two whose first step lowers
+    the loss on this case).
+    """
+    A, P = pb.poisson2d_problem(64)
+    Pt = pb.perturb_values(P, seed=5)
+    Ar, Pr, Ptr = rounded(A, dtype), rounded(P, dtype), rounded(Pt, dtype)
+    dA_, dP_ = to_dev(A, dtype), to_dev(P, dtype)
+    plan = ptap.symbolic(dA_, dP_)
+    Ct = ptap.numeric(plan, dA_, to_dev(Pt, dtype))
+    Pv = dP_.val.clone().requires_grad_(True)
+    lr, steps, hist = 1.0 / 32, 10, []
+    for _ in range(steps):
+        Pv.grad = None
+        loss = ((ptap.PtAP.apply(dA_.val, Pv, plan, dA_, dP_) - Ct) ** 2).sum()
+        loss.backward()
+        hist.append(loss.item())
+        with torch.no_grad():
+            Pv -= lr * Pv.grad
+    ref = _oracle_gd(Ar, Pr, Ptr, lr, steps)
+    assert all(y < x for x, y in zip(hist, hist[1:]))
+    assert hist[-1] < 0.05 * hist[0]
+    tol = 1e-9 if dtype == torch.float64 else 2e-3
+    for g, r in zip(hist, ref):
+        assert abs(g - r) <= tol * r, (hist, ref)
+
+
 @pytest.mark.parametrize("dtype", DTYPES)
 def test_batch_and_graph(dtype):
     probs = pb.batch_problems(seed=4, count=6, lo=8, hi=20)
