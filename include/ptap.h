@@ -87,8 +87,12 @@ typedef struct {
 /* Tuning knobs; zero selects the built-in default for a field. */
 typedef struct {
   int32_t mode;           /* PTAP_MODE_* */
-  int32_t chunk_entries;  /* C entries accumulated per CTA in owner mode */
-  int32_t block_threads;  /* threads per CTA of the numeric kernels */
+  int32_t chunk_entries;  /* C entries accumulated per CTA in owner mode: 64..32768 (class-program
+                             kernels; clamped so the accumulator fits shared memory, 24576 for
+                             FP64) or 64..16384 (general kernels); 0 = default */
+  int32_t block_threads;  /* threads per CTA of the numeric kernels: 64, 128, 256, or 512/1024
+                             for the class-program kernels (the general and batch kernels use
+                             at most 256); 0 = default 256 */
   int32_t group_lanes;    /* lanes that cooperate on one fine row: 4, 8, 16 or 32 */
   int32_t ap_slots;       /* hash slots per group for one row of A P */
   int32_t debug_checks;   /* nonzero: validate CSR inputs on the device */

@@ -26,11 +26,12 @@ DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "ptap_autotune.j
 CANDIDATES = [
     dict(),
     dict(specialize=8),
-    dict(specialize=4),
-    dict(specialize=16),
-    dict(chunk_entries=16384, specialize=8),
+    dict(specialize=8, block_threads=512, chunk_entries=16384),
+    dict(specialize=8, block_threads=1024, chunk_entries=32768),
+    dict(specialize=16, block_threads=1024, chunk_entries=32768),
+    dict(specialize=4, block_threads=1024, chunk_entries=32768),
+    dict(block_threads=512, chunk_entries=16384),
     dict(chunk_entries=4096),
-    dict(visit_block_log2=8),
     dict(class_programs=False),
     dict(mode=2, group_lanes=8, ap_slots=32),
 ]

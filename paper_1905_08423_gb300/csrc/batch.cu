@@ -95,6 +95,9 @@ static int batch_create_t(ptap_batch* b, ptap_plan* const* plans, const ptap_csr
       f.max_rows = std::max(p->max_chunk_rows, 1);
       f.prog_cap = (p->class_maxlen + 15) & ~15;
       f.maxr = std::max(p->class_maxr, 1);
+      f.work = nullptr;  // the batch has its own queue
+      f.chunk_order = nullptr;
+      f.rs_global = nullptr;
     }
     NumArgs<V>& a = h[q];
     a.A = CsrV<V>{A[q].nrows, A[q].ncols, A[q].row_ptr, A[q].col_idx, (const V*)A[q].val};
@@ -233,8 +236,7 @@ extern "C" int ptap_batch_create(ptap_plan* const* plans, const ptap_csr* A, con
   for (int32_t q = 0; q < count; ++q) {
     const ptap_plan* p = plans[q];
     if (!p || p->kind != 0 || p->dtype != p0->dtype) return PTAP_ERR_INVALID;
-    all_fast = all_fast && p->fast && p->cfg.mode == PTAP_MODE_OWNER &&
-               p->cfg.block_threads == p0->cfg.block_threads;
+    all_fast = all_fast && p->fast && p->cfg.mode == PTAP_MODE_OWNER;
     fast_ch = std::max(fast_ch, p->cfg.chunk_entries);
     fast_maxr = std::max(fast_maxr, p->class_maxr);
     fast_prog_cap = std::max(fast_prog_cap, (p->class_maxlen + 15) & ~15);
@@ -259,6 +261,7 @@ extern "C" int ptap_batch_create(ptap_plan* const* plans, const ptap_csr* A, con
   b->dtype = p0->dtype;
   b->count = count;
   b->cfg = p0->cfg;
+  b->cfg.block_threads = std::min(b->cfg.block_threads, 256);  // the batch kernels' bound
   b->max_chunk_rows = max_rows;
   b->fast = all_fast;
   b->fast_ch = fast_ch;

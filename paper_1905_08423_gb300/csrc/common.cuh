@@ -189,6 +189,10 @@ struct ptap_plan {
   // launch configuration of the numeric kernel, settled at symbolic time
   size_t num_smem = 0;
   int num_per_sm = 0;
+  // dynamic chunk schedule of the class-program kernels: a counter pair
+  // (zero between launches) and the chunks longest first
+  int32_t* work = nullptr;
+  int32_t* chunk_order = nullptr;
 
   // fine-row classes for the fast numeric path (classes.cu)
   int fast = 0;
@@ -200,6 +204,9 @@ struct ptap_plan {
 
   // plan-time specialised kernel (jit.cu); null when the interpreter runs
   void* jit_fn = nullptr;
+  void* jit_rs = nullptr;  // global scratch for the interpreted classes' rows of A P
+  void* interp_rs = nullptr;  // the same for the interpreter kernel, when shared memory is short
+  size_t jit_smem = 0;
   int jit_per_sm = 0, jit_classes = 0;
   double jit_coverage = 0.0, jit_ms = 0.0;
   uint8_t* class_pool = nullptr; // class programs (signatures), see classes.cu

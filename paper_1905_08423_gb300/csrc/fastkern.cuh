@@ -58,7 +58,26 @@ struct FastArgs {
   int32_t max_rows;
   int32_t prog_cap;  // bytes of program buffer per warp (multiple of 16)
   int32_t maxr;      // largest row of A P over the classes
+  // Optional dynamic schedule: when `work` is set, CTAs take chunks in the
+  // order `chunk_order` (longest first) from the counter work[0]; the last CTA
+  // to finish resets work[0] and work[1] to zero for the next launch.
+  int32_t* work;
+  const int32_t* chunk_order;
+  // Optional global scratch for the interpreter's rows of A P (32 * maxr
+  // values per warp of each resident CTA); null keeps them in shared memory.
+  V* rs_global;
 };
+
+// Adds v to *p, p in shared memory.  A relaxed reduction: the barrier that
+// ends the chunk orders it before the accumulator is read.  (The generated
+// code uses it; the interpreter keeps atomicAdd, which needs fewer registers
+// in its loops.)
+__device__ __forceinline__ void red_add(float* p, float v) {
+  asm volatile("red.shared.add.f32 [%0], %1;" ::"r"((unsigned)__cvta_generic_to_shared(p)), "f"(v) : "memory");
+}
+__device__ __forceinline__ void red_add(double* p, double v) {
+  asm volatile("red.shared.add.f64 [%0], %1;" ::"r"((unsigned)__cvta_generic_to_shared(p)), "d"(v) : "memory");
+}
 
 // Interpreter: 32 fine rows [f, min(f+32, f1)) of one class, one per lane.
 // R is the lane's row of A P, lane-major in shared memory (R[t*32 + lane]).
@@ -132,14 +151,15 @@ __device__ __forceinline__ void fast_piece(const FastArgs<V>& a, const uint8_t* 
   }
 }
 
-// Shared-memory carve-up: accumulator | interpreter R rows | row offsets |
-// per-warp program buffers; every region 16-byte aligned.
+// Shared-memory carve-up: accumulator | interpreter R rows (unless they live
+// in global scratch) | row offsets | per-warp program buffers; every region
+// 16-byte aligned.
 template <typename V>
 __host__ __device__ inline size_t fast_smem_bytes(int CH, int threads, int maxr, int max_rows,
-                                                  int prog_cap) {
+                                                  int prog_cap, bool rs_in_smem = true) {
   const int CHa = (CH + 3) & ~3;
   const int rows = (max_rows + 1 + 3) & ~3;
-  return ((size_t)CHa + (size_t)threads * maxr) * sizeof(V) + (size_t)rows * 4 +
+  return ((size_t)CHa + (rs_in_smem ? (size_t)threads * maxr : 0)) * sizeof(V) + (size_t)rows * 4 +
          (size_t)(threads / 32) * prog_cap;
 }
 
@@ -151,12 +171,18 @@ struct FastSmem {
   V* Rs;
   int32_t* roff;
   uint8_t* prog;
-  __device__ FastSmem(unsigned char* raw, int CH, int maxr, int max_rows, int prog_cap) {
+  __device__ FastSmem(unsigned char* raw, int CH, int maxr, int max_rows, int prog_cap,
+                      V* rs_global = nullptr) {
     const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const int CHa = (CH + 3) & ~3;
     acc = (V*)raw;
-    Rs = acc + CHa + (size_t)warp * 32 * maxr;
-    roff = (int32_t*)(acc + CHa + (size_t)nwarps * 32 * maxr);
+    if (rs_global) {
+      Rs = rs_global + ((size_t)blockIdx.x * nwarps + warp) * 32 * maxr;
+      roff = (int32_t*)(acc + CHa);
+    } else {
+      Rs = acc + CHa + (size_t)warp * 32 * maxr;
+      roff = (int32_t*)(acc + CHa + (size_t)nwarps * 32 * maxr);
+    }
     prog = (uint8_t*)(roff + ((max_rows + 1 + 3) & ~3)) + warp * prog_cap;
   }
 };
@@ -200,8 +226,30 @@ __device__ __forceinline__ void fast_chunk(const FastArgs<V>& a, int32_t c, Fast
 template <typename V, typename Special>
 __device__ __forceinline__ void fast_kernel_body(const FastArgs<V>& a, Special special) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  FastSmem<V> sm(smraw, a.CH, a.maxr, a.max_rows, a.prog_cap);
-  for (int32_t c = blockIdx.x; c < a.nchunks; c += gridDim.x) fast_chunk<V>(a, c, sm, special);
+  __shared__ int32_t next;
+  FastSmem<V> sm(smraw, a.CH, a.maxr, a.max_rows, a.prog_cap, a.rs_global);
+  if (!a.work) {
+    for (int32_t c = blockIdx.x; c < a.nchunks; c += gridDim.x) fast_chunk<V>(a, c, sm, special);
+    return;
+  }
+  // chunks from a shared counter, longest first: no CTA idles while others
+  // still hold several chunks
+  for (;;) {
+    if (threadIdx.x == 0) next = atomicAdd(&a.work[0], 1);
+    __syncthreads();
+    const int32_t t = next;
+    __syncthreads();
+    if (t >= a.nchunks) break;
+    fast_chunk<V>(a, a.chunk_order ? a.chunk_order[t] : t, sm, special);
+  }
+  // the last CTA to leave puts the counters back to zero for the next launch
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(&a.work[1], 1) == (int32_t)gridDim.x - 1) {
+      atomicExch(&a.work[0], 0);
+      atomicExch(&a.work[1], 0);
+    }
+  }
 }
 
 }  // namespace ptapk

@@ -3,6 +3,7 @@
 // kernel and launches either it or the plan's NVRTC-specialised kernel
 // (jit.cu), whose classes run as straight-line code.
 #include <algorithm>
+#include <vector>
 
 #include "common.cuh"
 #include "fastkern.cuh"
@@ -22,8 +23,10 @@ struct NoSpecial {
 };
 }  // namespace
 
-template <typename V>
-__global__ void __launch_bounds__(256) k_numeric_fast(FastArgs<V> a) {
+// MaxT: the largest CTA the instantiation is compiled for (256, or 1024 for
+// the large-chunk configurations, which cap registers at 64).
+template <typename V, int MaxT>
+__global__ void __launch_bounds__(MaxT) k_numeric_fast(FastArgs<V> a) {
   ptapk::fast_kernel_body<V>(a, NoSpecial());
 }
 
@@ -46,27 +49,80 @@ static FastArgs<V> fast_args(ptap_plan* p, const ptap_csr* A, const ptap_csr* P,
   a.max_rows = std::max(p->max_chunk_rows, 1);
   a.prog_cap = (p->class_maxlen + 15) & ~15;
   a.maxr = std::max(p->class_maxr, 1);
+  a.work = p->work;
+  a.chunk_order = p->chunk_order;
+  a.rs_global = (V*)p->interp_rs;
   return a;
 }
 
 template <typename V>
-static size_t fast_smem(const ptap_plan* p) {
+static size_t fast_smem(const ptap_plan* p, bool rs_in_smem = true) {
   return ptapk::fast_smem_bytes<V>(p->cfg.chunk_entries, p->cfg.block_threads, std::max(p->class_maxr, 1),
-                                   std::max(p->max_chunk_rows, 1), (p->class_maxlen + 15) & ~15);
+                                   std::max(p->max_chunk_rows, 1), (p->class_maxlen + 15) & ~15, rs_in_smem);
 }
 
-size_t fast_smem_for(const ptap_plan* p) {
-  return p->dtype == PTAP_F64 ? fast_smem<double>(p) : fast_smem<float>(p);
+size_t fast_smem_for(const ptap_plan* p, bool rs_in_smem) {
+  return p->dtype == PTAP_F64 ? fast_smem<double>(p, rs_in_smem) : fast_smem<float>(p, rs_in_smem);
+}
+
+// The dynamic schedule: chunks ordered by fine-row visits, longest first, and
+// a zeroed counter pair.
+static int prepare_schedule(ptap_plan* p) {
+  if (p->work) return PTAP_OK;
+  cudaStream_t s = p->stream;
+  std::vector<int32_t> fptr(p->nchunks + 1);
+  PTAP_CUDA(cudaMemcpyAsync(fptr.data(), p->chunk_fptr, fptr.size() * sizeof(int32_t), cudaMemcpyDeviceToHost,
+                            s));
+  PTAP_CUDA(cudaStreamSynchronize(s));
+  std::vector<int32_t> order(p->nchunks);
+  for (int32_t c = 0; c < p->nchunks; ++c) order[c] = c;
+  std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) {
+    return fptr[x + 1] - fptr[x] > fptr[y + 1] - fptr[y];
+  });
+  PTAP_TRY(p->mem.get_n(&p->chunk_order, std::max<int64_t>(p->nchunks, 1)));
+  PTAP_TRY(p->mem.get_n(&p->work, 2));
+  PTAP_CUDA(cudaMemcpyAsync(p->chunk_order, order.data(), order.size() * sizeof(int32_t),
+                            cudaMemcpyHostToDevice, s));
+  PTAP_CUDA(cudaMemsetAsync(p->work, 0, 2 * sizeof(int32_t), s));
+  PTAP_CUDA(cudaStreamSynchronize(s));
+  return PTAP_OK;
 }
 
 template <typename V>
-static int prepare_fast_t(ptap_plan* p) {
-  const size_t smem = fast_smem<V>(p);
-  PTAP_CUDA(cudaFuncSetAttribute(k_numeric_fast<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+static auto fast_kernel_for(const ptap_plan* p) {
+  return p->cfg.block_threads > 256 ? k_numeric_fast<V, 1024> : k_numeric_fast<V, 256>;
+}
+
+// Occupancy of the interpreter kernel for a dynamic shared-memory size; 0 if
+// it cannot launch.
+template <typename V>
+static int fast_occupancy(const ptap_plan* p, size_t smem) {
+  int dev = 0, optin = 0;
+  PTAP_CUDA(cudaGetDevice(&dev));
+  PTAP_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  if (smem > (size_t)optin) return 0;
+  auto k = fast_kernel_for<V>(p);
+  PTAP_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
-  PTAP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_numeric_fast<V>, p->cfg.block_threads,
-                                                          smem));
-  if (per_sm < 1) return PTAP_ERR_INVALID;
+  PTAP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, p->cfg.block_threads, smem));
+  return per_sm;
+}
+
+// The interpreter keeps its rows of A P in shared memory when they fit beside
+// the accumulator; otherwise (large CTAs and chunks) in a global scratch of
+// 32 * maxr values per warp of each resident CTA.
+template <typename V>
+static int prepare_fast_t(ptap_plan* p) {
+  size_t smem = fast_smem<V>(p, true);
+  int per_sm = fast_occupancy<V>(p, smem);
+  if (per_sm < 1) {
+    smem = fast_smem<V>(p, false);
+    per_sm = fast_occupancy<V>(p, smem);
+    if (per_sm < 1) return PTAP_ERR_INVALID;
+    const int64_t ctas = std::min<int64_t>(std::max(p->nchunks, 1), (int64_t)num_sms() * per_sm);
+    PTAP_TRY(p->mem.get(&p->interp_rs, (size_t)ctas * p->cfg.block_threads * std::max(p->class_maxr, 1) *
+                                           sizeof(V)));
+  }
   p->num_smem = smem;
   p->num_per_sm = per_sm;
   return PTAP_OK;
@@ -77,21 +133,23 @@ int jit_launch(ptap_plan* p, const void* args, int grid, cudaStream_t s);
 
 int prepare_fast(ptap_plan* p) {
   PTAP_TRY(p->dtype == PTAP_F64 ? prepare_fast_t<double>(p) : prepare_fast_t<float>(p));
+  PTAP_TRY(prepare_schedule(p));
   if (p->cfg.jit) jit_prepare(p);  // optional: the interpreter runs if it fails
   return PTAP_OK;
 }
 
 template <typename V>
 static int launch_fast_t(ptap_plan* p, const ptap_csr* A, const ptap_csr* P, void* C, cudaStream_t s) {
-  const FastArgs<V> args = fast_args<V>(p, A, P, C);
+  FastArgs<V> args = fast_args<V>(p, A, P, C);
   if (p->jit_fn) {
     const int grid = (int)std::min<int64_t>(p->nchunks, (int64_t)num_sms() * p->jit_per_sm);
     if (grid <= 0) return PTAP_OK;
+    args.rs_global = (V*)p->jit_rs;
     return jit_launch(p, &args, grid, s);
   }
   const int grid = (int)std::min<int64_t>(p->nchunks, (int64_t)num_sms() * p->num_per_sm);
   if (grid <= 0) return PTAP_OK;
-  k_numeric_fast<V><<<grid, p->cfg.block_threads, p->num_smem, s>>>(args);
+  fast_kernel_for<V>(p)<<<grid, p->cfg.block_threads, p->num_smem, s>>>(args);
   PTAP_LAUNCHED();
   return PTAP_OK;
 }

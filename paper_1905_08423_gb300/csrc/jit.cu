@@ -34,7 +34,7 @@
 
 namespace ptap {
 
-size_t fast_smem_for(const ptap_plan* p);
+size_t fast_smem_for(const ptap_plan* p, bool rs_in_smem);
 
 namespace {
 
@@ -63,6 +63,7 @@ Nvrtc g_rtc;
 Driver g_drv;
 bool g_loaded = false;
 std::map<std::pair<int, uint64_t>, CUfunction> g_cache;  // (device, source hash) -> function
+std::map<void*, int> g_smem_attr;  // largest dynamic shared memory set on each function
 
 template <class F>
 bool sym(void* lib, const char* name, F& f) {
@@ -167,7 +168,7 @@ std::string gen_class(int cls, const uint8_t* g) {
           "    if (valid && i >= i0 && i < i1) {\n      V* c = acc + roff[i - i0];\n"
           "      const unsigned char* sg = sg_%d + s * %d;\n",
           pI, pI, cls, r);
-  for (int t = 0; t < r; ++t) appendf(o, "      atomicAdd(c + sg[%d], w * R%d);\n", t, t);
+  for (int t = 0; t < r; ++t) appendf(o, "      red_add(c + sg[%d], w * R%d);\n", t, t);
   o += "    }\n  }\n}\n";
   return o;
 }
@@ -220,9 +221,11 @@ int jit_prepare(ptap_plan* p) {
     snprintf(buf, sizeof buf, "      case %d: cls_%d(a, f, f1, i0, i1, acc, roff); return true;\n", k, k);
     src += buf;
   }
-  src += "      default: return false;\n    }\n  }\n};\n"
-         "extern \"C\" __global__ void __launch_bounds__(256, 4) ptap_jit_numeric(FastArgs<V> a) {\n"
-         "  fast_kernel_body<V>(a, Special());\n}\n";
+  src += "      default: return false;\n    }\n  }\n};\n";
+  // 64 registers a thread: 1024 threads of resident CTAs per SM
+  appendf(src, "extern \"C\" __global__ void __launch_bounds__(%d, %d) ptap_jit_numeric(FastArgs<V> a) {\n",
+          p->cfg.block_threads, std::max(1, 1024 / p->cfg.block_threads));
+  src += "  fast_kernel_body<V>(a, Special());\n}\n";
   int dev = 0;
   PTAP_CUDA(cudaGetDevice(&dev));
   const uint64_t key = fnv64(src) ^ fnv64(kFastKernSource);
@@ -259,12 +262,26 @@ int jit_prepare(ptap_plan* p) {
     if (g_drv.get_fn(&fn, mod, "ptap_jit_numeric") != CUDA_SUCCESS) return PTAP_ERR_CUDA;
     g_cache[{dev, key}] = fn;
   }
-  const size_t smem = fast_smem_for(p);
-  if (g_drv.set_attr(fn, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, (int)smem) != CUDA_SUCCESS)
-    return PTAP_ERR_CUDA;
+  // The compiled classes keep their rows of A P in registers, so the
+  // interpreted ones use a global scratch instead of shared memory: the
+  // accumulator alone sets the shared-memory footprint.
+  const size_t smem = fast_smem_for(p, false);
+  int& attr = g_smem_attr[(void*)fn];  // the module is shared by plans: the attribute only grows
+  if ((int)smem > attr) {
+    if (g_drv.set_attr(fn, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, (int)smem) != CUDA_SUCCESS)
+      return PTAP_ERR_CUDA;
+    attr = (int)smem;
+  }
   int per_sm = 0;
   if (g_drv.occupancy(&per_sm, fn, p->cfg.block_threads, smem) != CUDA_SUCCESS || per_sm < 1)
     return PTAP_ERR_CUDA;
+  const size_t vb = p->dtype == PTAP_F64 ? 8 : 4;
+  const int64_t ctas = std::min<int64_t>(p->nchunks, (int64_t)num_sms() * per_sm);
+  void* rs = nullptr;
+  PTAP_TRY(p->mem.get(&rs, (size_t)std::max<int64_t>(ctas, 1) * p->cfg.block_threads *
+                               std::max(p->class_maxr, 1) * vb));
+  p->jit_rs = rs;
+  p->jit_smem = smem;
   p->jit_fn = (void*)fn;
   p->jit_per_sm = per_sm;
   p->jit_classes = (int)hot.size();
@@ -275,7 +292,7 @@ int jit_prepare(ptap_plan* p) {
 
 int jit_launch(ptap_plan* p, const void* args, int grid, cudaStream_t s) {
   void* params[1] = {const_cast<void*>(args)};
-  if (g_drv.launch((CUfunction)p->jit_fn, grid, 1, 1, p->cfg.block_threads, 1, 1, (unsigned)p->num_smem,
+  if (g_drv.launch((CUfunction)p->jit_fn, grid, 1, 1, p->cfg.block_threads, 1, 1, (unsigned)p->jit_smem,
                    (CUstream)s, params, nullptr) != CUDA_SUCCESS)
     return PTAP_ERR_CUDA;
   return PTAP_OK;

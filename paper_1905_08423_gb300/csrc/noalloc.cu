@@ -89,7 +89,8 @@ template <typename V, int G>
 int launch(ptap_plan* const* plans, const ptap_csr* A, const ptap_csr* P, void* const* C,
            int32_t count, int64_t nitems, int32_t max_rows, unsigned char* dscratch,
            cudaStream_t s) {
-  const Config& c = plans[0]->cfg;
+  Config c = plans[0]->cfg;
+  c.block_threads = std::min(c.block_threads, 256);  // the kernel's bound
   NumArgs<V>* desc = (NumArgs<V>*)g_host_stage;
   int32_t* items = (int32_t*)(g_host_stage + (kItemsOffset - kDescOffset));
   int64_t t = 0;

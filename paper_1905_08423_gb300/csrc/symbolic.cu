@@ -696,6 +696,10 @@ int symbolic_prologue(const ptap_csr* A, const ptap_csr* P, const ptap_config* c
   p->nnz_p = P->nnz;
   p->stream = s;
   p->cfg = resolve_config(cfg);
+  if (kind != 0) {  // the two-step kernels: CTAs of at most 256 threads
+    p->cfg.block_threads = std::min(p->cfg.block_threads, 256);
+    if (p->cfg.chunk_entries > 16384) p->cfg.chunk_entries = 16384;
+  }
   p->mem.init(alloc, s);
   int rc = check_ends(A, s);
   if (rc == PTAP_OK) rc = check_ends(P, s);
@@ -713,6 +717,19 @@ int symbolic_prologue(const ptap_csr* A, const ptap_csr* P, const ptap_config* c
   }
   *out = p;
   return PTAP_OK;
+}
+
+// Largest chunk (entries) whose accumulator, with room for the row offsets and
+// program buffers, fits the device's opt-in shared memory; a multiple of 1024.
+static int fast_chunk_limit(int vb) {
+  int dev = 0, optin = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return 8192;
+  }
+  const int n = (optin - 32 * 1024) / vb;
+  return std::max(1024, std::min(32768, n & ~1023));
 }
 
 static int symbolic_body(ptap_plan* p, const ptap_csr* A, const ptap_csr* P) {
@@ -736,23 +753,31 @@ static int symbolic_body(ptap_plan* p, const ptap_csr* A, const ptap_csr* P) {
   // Owner-mode schedule.  With per-class programs the on-chip accumulator
   // needs no column indices, so chunks can be larger (fewer fine rows are
   // visited by two chunks); without them the general kernel's default applies.
+  // The class-program kernels accept CTAs of up to 1024 threads and chunks up
+  // to 32768 entries (bounded by shared memory for the value type); the
+  // general kernels keep at most 256 threads and 16384 entries.
   const bool user_ch = p->cfg.chunk_entries > 0;
-  const int ch_fast = 8192, ch_general = 4096;
+  const int ch_fast = 8192, ch_general = 4096, ch_general_max = 16384;
+  const int ch_fast_max = fast_chunk_limit(p->dtype == PTAP_F64 ? 8 : 4);
   const bool try_fast = p->cfg.class_programs && p->cfg.mode == PTAP_MODE_OWNER &&
                         !p->cfg.force_spill && (!user_ch || p->cfg.chunk_entries >= 256);
-  p->cfg.chunk_entries = user_ch ? p->cfg.chunk_entries : (try_fast ? ch_fast : ch_general);
+  const int user_value = p->cfg.chunk_entries;
+  p->cfg.chunk_entries = user_ch ? std::min(user_value, try_fast ? ch_fast_max : ch_general_max)
+                                 : (try_fast ? ch_fast : ch_general);
   PTAP_TRY(build_schedule(p, P, s));
   if (try_fast) {
     PTAP_TRY(build_classes(p, A, P, s));
-    if (!p->fast && !user_ch && p->cfg.chunk_entries != ch_general) {
+    const int general_ch = user_ch ? std::min(user_value, ch_general_max) : ch_general;
+    if (!p->fast && p->cfg.chunk_entries != general_ch) {
       p->mem.put(p->chunk_row);
       p->mem.put(p->chunk_fptr);
       p->mem.put(p->chunk_frows);
       p->chunk_row = p->chunk_fptr = p->chunk_frows = nullptr;
-      p->cfg.chunk_entries = ch_general;
+      p->cfg.chunk_entries = general_ch;
       PTAP_TRY(build_schedule(p, P, s));
     }
   }
+  if (!p->fast) p->cfg.block_threads = std::min(p->cfg.block_threads, 256);
   PTAP_TRY(prepare_numeric(p));
   PTAP_CUDA(cudaStreamSynchronize(s));
   int32_t st = 0;

@@ -67,7 +67,32 @@ CONFIGS = [
     dict(visit_block_log2=6),                     # class programs in 64-row blocks
     dict(visit_block_log2=8, chunk_entries=2048),
     dict(specialize=4, chunk_entries=1024),       # compiled classes and interpreted ones mixed
+    dict(block_threads=1024, chunk_entries=32768),  # interpreter, rows of A P in global scratch
+    dict(block_threads=512, class_programs=False),  # general kernel: CTA clamped to 256
 ]
+
+
+LARGE_CTA = [
+    dict(specialize=8, block_threads=512, chunk_entries=16384),
+    dict(specialize=4, block_threads=1024, chunk_entries=32768),
+    dict(block_threads=1024, chunk_entries=32768),
+    dict(block_threads=512, chunk_entries=12288),
+]
+
+
+@pytest.mark.parametrize("cfg", LARGE_CTA, ids=[str(c) for c in LARGE_CTA])
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_large_ctas_many_chunks(cfg, dtype):
+    """CTAs of 512/1024 threads with large chunks, over many chunks (dynamic schedule)."""
+    A, P = pb.model_problem(63)
+    plan, _ = run_and_check(A, P, dtype, ptap.make_config(**cfg))
+    st = plan.stats()
+    assert st["fast_path"] == 1 and st["block_threads"] == cfg["block_threads"]
+    assert st["n_chunks"] > 8
+    if dtype == torch.float64:
+        assert st["chunk_entries"] <= 24576     # the accumulator must fit shared memory
+    else:
+        assert st["chunk_entries"] == cfg["chunk_entries"]
 
 
 @pytest.mark.parametrize("cfg", CONFIGS, ids=[str(c) for c in CONFIGS])
@@ -77,6 +102,14 @@ def test_configs(cfg, dtype):
     run_and_check(A, P, dtype, ptap.make_config(**cfg))
     A2, P2 = pb.model_problem(17)
     run_and_check(A2, P2, dtype, ptap.make_config(**cfg))
+
+
+def test_two_step_with_large_cta_config():
+    """A configuration tuned for the class-program kernels also drives the two-step path."""
+    A, P = pb.algebraic_problem(12, seed=5)
+    cfg = ptap.make_config(specialize=8, block_threads=1024, chunk_entries=32768)
+    plan, _ = run_and_check(A, P, torch.float32, config=cfg, two_step=True)
+    assert plan.stats()["block_threads"] == 256
 
 
 @pytest.mark.parametrize("dtype", DTYPES)
