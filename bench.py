@@ -583,9 +583,12 @@ def main():
                              "fast_path": st["fast_path"], "classes": st["n_classes"],
                              "specialized_classes": st["n_specialized"],
                              "specialized_share": st["specialized_permille"] / 1000.0,
+                             "specialize_ms": round(st["specialize_us"] / 1000.0, 1),
                              "chunk_entries": st["chunk_entries"], "chunks": st["n_chunks"],
                              "fine_row_visits": st["chunk_fine_rows"]},
            "symbolic_ms": round(sym_ms, 2),
+           "symbolic_first_ms": (round(dict((json.dumps(c, sort_keys=True), t) for c, t in tuned.symbolic_ms)
+                                       .get(json.dumps(cfg_kw, sort_keys=True), sym_ms), 2) if tuned else None),
            "c_nnz_per_s": round(nnz_c / (ms_step * 1e-3), 1),
            "gpu_launches": args.steps,
            "clocks": clocks}

@@ -29,6 +29,7 @@ CANDIDATES = [
     dict(specialize=8, block_threads=512, chunk_entries=16384),
     dict(specialize=8, block_threads=1024, chunk_entries=32768),
     dict(specialize=16, block_threads=1024, chunk_entries=32768),
+    dict(specialize=32, block_threads=1024, chunk_entries=32768),
     dict(specialize=4, block_threads=1024, chunk_entries=32768),
     dict(block_threads=512, chunk_entries=16384),
     dict(chunk_entries=4096),
@@ -73,6 +74,7 @@ class TuneResult:
     ms: float
     trials: list = field(default_factory=list)  # (config, ms or error string)
     cached: bool = False
+    symbolic_ms: list = field(default_factory=list)  # (config, symbolic ms incl. any code generation)
 
 
 def _time_numeric(ptap, plan, A, P, C, reps: int, warmup: int) -> float:
@@ -107,10 +109,15 @@ def tune(A, P, candidates=None, reps: int = 5, warmup: int = 2, cache_path: str 
     if use_cache and key in cache:
         e = cache[key]
         return TuneResult(dict(e["config"]), float(e["ms"]), [], cached=True)
-    best, best_ms, trials = None, float("inf"), []
+    best, best_ms, trials, sym = None, float("inf"), [], []
     for cand in (candidates or CANDIDATES):
         try:
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
             plan = ptap.symbolic(A, P, ptap.make_config(**cand))
+            e1.record()
+            torch.cuda.synchronize()
+            sym.append((cand, e0.elapsed_time(e1)))
             C = torch.empty(plan.nnz, dtype=plan.torch_dtype, device=A.row_ptr.device)
             ms = _time_numeric(ptap, plan, A, P, C, reps, warmup)
             plan.destroy()
@@ -127,4 +134,4 @@ def tune(A, P, candidates=None, reps: int = 5, warmup: int = 2, cache_path: str 
         cache = load_cache(cache_path)
         cache[key] = {"config": best, "ms": best_ms}
         save_cache(cache, cache_path)
-    return TuneResult(best, best_ms, trials)
+    return TuneResult(best, best_ms, trials, symbolic_ms=sym)

@@ -45,7 +45,7 @@ __global__ void __launch_bounds__(256) k_batch_owner(const NumArgs<V>* __restric
 struct NoSpecial {
   template <typename V>
   __device__ bool operator()(const ptapk::FastArgs<V>&, int32_t, int32_t, int32_t, int32_t, int32_t, V*,
-                             const int32_t*) const {
+                             const int32_t*, int32_t) const {
     return false;
   }
 };
@@ -98,6 +98,7 @@ static int batch_create_t(ptap_batch* b, ptap_plan* const* plans, const ptap_csr
       f.work = nullptr;  // the batch has its own queue
       f.chunk_order = nullptr;
       f.rs_global = nullptr;
+      f.jit_slot = nullptr;
     }
     NumArgs<V>& a = h[q];
     a.A = CsrV<V>{A[q].nrows, A[q].ncols, A[q].row_ptr, A[q].col_idx, (const V*)A[q].val};

@@ -205,6 +205,7 @@ struct ptap_plan {
   // plan-time specialised kernel (jit.cu); null when the interpreter runs
   void* jit_fn = nullptr;
   void* jit_rs = nullptr;  // global scratch for the interpreted classes' rows of A P
+  int32_t* jit_slot = nullptr;  // [nclasses] compiled-code number of each class, or -1
   void* interp_rs = nullptr;  // the same for the interpreter kernel, when shared memory is short
   size_t jit_smem = 0;
   int jit_per_sm = 0, jit_classes = 0;

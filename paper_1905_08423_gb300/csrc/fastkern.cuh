@@ -66,6 +66,9 @@ struct FastArgs {
   // Optional global scratch for the interpreter's rows of A P (32 * maxr
   // values per warp of each resident CTA); null keeps them in shared memory.
   V* rs_global;
+  // Plan-time specialised code: the compiled-code number of each class, or
+  // -1 (null without compiled code).
+  const int32_t* jit_slot;
 };
 
 // Adds v to *p, p in shared memory.  A relaxed reduction: the barrier that
@@ -84,11 +87,10 @@ __device__ __forceinline__ void red_add(double* p, double v) {
 template <typename V>
 __device__ __forceinline__ void fast_piece(const FastArgs<V>& a, const uint8_t* prog, V* R, int32_t f,
                                            int32_t f1, int32_t i0, int32_t i1, V* acc,
-                                           const int32_t* roff) {
+                                           const int32_t* roff, int32_t I) {
   const int lane = threadIdx.x & 31;
   const bool valid = f + lane < f1;
-  // lanes past the piece's end redo its first row and add nothing
-  const int32_t I = a.frows[valid ? f + lane : f];
+  // lanes past the piece's end redo its first row (I) and add nothing
   const int na = prog[0], r = prog[1], pI = prog[2];
   const uint8_t* pa_sec = prog + 8;
   const uint64_t* t_sec = (const uint64_t*)(prog + 8 + ((na + 7) & ~7));
@@ -187,9 +189,10 @@ struct FastSmem {
   }
 };
 
-// One chunk c of a product.  `special(a, cls, f, f1, i0, i1, acc, roff)` runs
-// a piece of a class it has straight-line code for and returns true;
-// otherwise the interpreter runs it from the class's program.
+// One chunk c of a product.  `special(a, cls, f, f1, i0, i1, acc, roff, I)`
+// runs a piece of a class it has straight-line code for and returns true;
+// otherwise the interpreter runs it from the class's program.  I is the
+// lane's fine row of the piece, loaded one piece ahead.
 template <typename V, typename Special>
 __device__ __forceinline__ void fast_chunk(const FastArgs<V>& a, int32_t c, FastSmem<V>& sm,
                                            Special special) {
@@ -204,18 +207,42 @@ __device__ __forceinline__ void fast_chunk(const FastArgs<V>& a, int32_t c, Fast
   // the chunk's pieces (<= 32 rows of one class) go round-robin to the warps
   int32_t loaded = -1;
   const int32_t pe = a.chunk_piece[c + 1];
-  for (int32_t pc = a.chunk_piece[c] + warp; pc < pe; pc += nwarps) {
-    const int32_t meta = a.piece_meta[pc], f0 = a.piece_f0[pc];
-    const int32_t cls = meta >> 6, f1 = f0 + (meta & 63);
-    if (special(a, cls, f0, f1, i0, i1, acc, roff)) continue;
-    if (cls != loaded) {
-      __syncwarp();
-      const uint8_t* src = a.pool + a.class_off[cls];
-      for (int x = lane; x < a.prog_cap; x += 32) sm.prog[x] = src[x];
-      __syncwarp();
-      loaded = cls;
+  int32_t pc = a.chunk_piece[c] + warp;
+  // software pipeline over this warp's pieces: the descriptor two pieces
+  // ahead and the fine row one piece ahead are loaded while a piece runs
+  int32_t meta = 0, f0 = 0, metan = 0, f0n = 0, I = 0;
+  if (pc < pe) {
+    meta = a.piece_meta[pc];
+    f0 = a.piece_f0[pc];
+  }
+  if (pc + nwarps < pe) {
+    metan = a.piece_meta[pc + nwarps];
+    f0n = a.piece_f0[pc + nwarps];
+  }
+  if (pc < pe) I = a.frows[f0 + lane < f0 + (meta & 63) ? f0 + lane : f0];
+  for (; pc < pe; pc += nwarps) {
+    int32_t In = 0, metann = 0, f0nn = 0;
+    if (pc + nwarps < pe) In = a.frows[f0n + lane < f0n + (metan & 63) ? f0n + lane : f0n];
+    if (pc + 2 * nwarps < pe) {
+      metann = a.piece_meta[pc + 2 * nwarps];
+      f0nn = a.piece_f0[pc + 2 * nwarps];
     }
-    fast_piece<V>(a, sm.prog, sm.Rs, f0, f1, i0, i1, acc, roff);
+    const int32_t cls = meta >> 6, f1 = f0 + (meta & 63);
+    if (!special(a, cls, f0, f1, i0, i1, acc, roff, I)) {
+      if (cls != loaded) {
+        __syncwarp();
+        const uint8_t* src = a.pool + a.class_off[cls];
+        for (int x = lane; x < a.prog_cap; x += 32) sm.prog[x] = src[x];
+        __syncwarp();
+        loaded = cls;
+      }
+      fast_piece<V>(a, sm.prog, sm.Rs, f0, f1, i0, i1, acc, roff, I);
+    }
+    meta = metan;
+    f0 = f0n;
+    metan = metann;
+    f0n = f0nn;
+    I = In;
   }
   __syncthreads();
   for (int t = threadIdx.x; t < nnz; t += blockDim.x) a.c_val[base + t] = acc[t];

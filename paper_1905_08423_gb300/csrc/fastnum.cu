@@ -17,7 +17,7 @@ namespace {
 struct NoSpecial {
   template <typename V>
   __device__ bool operator()(const FastArgs<V>&, int32_t, int32_t, int32_t, int32_t, int32_t, V*,
-                             const int32_t*) const {
+                             const int32_t*, int32_t) const {
     return false;
   }
 };
@@ -52,6 +52,7 @@ static FastArgs<V> fast_args(ptap_plan* p, const ptap_csr* A, const ptap_csr* P,
   a.work = p->work;
   a.chunk_order = p->chunk_order;
   a.rs_global = (V*)p->interp_rs;
+  a.jit_slot = p->jit_slot;
   return a;
 }
 

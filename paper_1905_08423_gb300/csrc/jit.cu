@@ -15,13 +15,19 @@
 // NVRTC and the driver API are reached through dlopen and the runtime's
 // driver entry points, so the library loads (and simply runs the interpreter)
 // where either is missing.  Compiled modules are kept for the life of the
-// process, keyed by device and source, and shared between plans.
+// process, keyed by device and source, and shared between plans; their cubins
+// are also cached on disk (see cache_dir) so that a later process with the
+// same classes skips the compile.
 #include <cuda.h>
 #include <dlfcn.h>
+#include <sys/stat.h>
+#include <unistd.h>
 #include <nvrtc.h>
 
 #include <algorithm>
 #include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
 #include <chrono>
 #include <map>
 #include <mutex>
@@ -47,6 +53,7 @@ struct Nvrtc {
   decltype(&nvrtcGetCUBINSize) cubin_size = nullptr;
   decltype(&nvrtcGetCUBIN) cubin = nullptr;
   decltype(&nvrtcDestroyProgram) destroy = nullptr;
+  decltype(&nvrtcVersion) version = nullptr;
 };
 
 struct Driver {
@@ -94,11 +101,48 @@ void load_apis() {
     g_rtc.ok = sym(lib, "nvrtcCreateProgram", g_rtc.create) && sym(lib, "nvrtcCompileProgram", g_rtc.compile) &&
                sym(lib, "nvrtcGetProgramLogSize", g_rtc.log_size) && sym(lib, "nvrtcGetProgramLog", g_rtc.log) &&
                sym(lib, "nvrtcGetCUBINSize", g_rtc.cubin_size) && sym(lib, "nvrtcGetCUBIN", g_rtc.cubin) &&
-               sym(lib, "nvrtcDestroyProgram", g_rtc.destroy);
+               sym(lib, "nvrtcDestroyProgram", g_rtc.destroy) && sym(lib, "nvrtcVersion", g_rtc.version);
   g_drv.ok = drv("cuModuleLoadData", g_drv.load) && drv("cuModuleGetFunction", g_drv.get_fn) &&
              drv("cuFuncSetAttribute", g_drv.set_attr) &&
              drv("cuOccupancyMaxActiveBlocksPerMultiprocessor", g_drv.occupancy) &&
              drv("cuLaunchKernel", g_drv.launch);
+}
+
+// Compiled modules also persist across processes, as cubin files named by
+// the hash of everything that determines them: PTAP_JIT_CACHE names the
+// directory (set but empty: no disk cache); by default $XDG_CACHE_HOME/ptap,
+// else $HOME/.cache/ptap.  A file that fails to load is compiled again.
+std::string cache_dir() {
+  if (const char* d = getenv("PTAP_JIT_CACHE")) return d;
+  if (const char* x = getenv("XDG_CACHE_HOME"); x && *x) return std::string(x) + "/ptap";
+  if (const char* h = getenv("HOME"); h && *h) return std::string(h) + "/.cache/ptap";
+  return "";
+}
+
+bool read_file(const std::string& path, std::vector<char>& out) {
+  FILE* f = fopen(path.c_str(), "rb");
+  if (!f) return false;
+  std::vector<char> buf;
+  char tmp[65536];
+  size_t n;
+  while ((n = fread(tmp, 1, sizeof tmp, f)) > 0) buf.insert(buf.end(), tmp, tmp + n);
+  fclose(f);
+  if (buf.empty()) return false;
+  out.swap(buf);
+  return true;
+}
+
+// mkdir -p, then write to a private temporary name and rename into place, so
+// readers never see a partial file.  Failures only cost the next process a compile.
+void write_file_atomic(const std::string& dir, const std::string& name, const std::vector<char>& data) {
+  for (size_t i = 1; i <= dir.size(); ++i)
+    if (i == dir.size() || dir[i] == '/') mkdir(dir.substr(0, i).c_str(), 0755);
+  const std::string path = dir + "/" + name;
+  const std::string tmp = path + ".tmp" + std::to_string((long long)getpid());
+  FILE* f = fopen(tmp.c_str(), "wb");
+  if (!f) return;
+  const bool ok = fwrite(data.data(), 1, data.size(), f) == data.size();
+  if (fclose(f) != 0 || !ok || rename(tmp.c_str(), path.c_str()) != 0) remove(tmp.c_str());
 }
 
 uint64_t fnv64(const std::string& s) {
@@ -145,10 +189,10 @@ std::string gen_class(int cls, const uint8_t* g) {
   o += "};\n";
   appendf(o,
           "__device__ __forceinline__ void cls_%d(const FastArgs<V>& a, int32_t f, int32_t f1, int32_t i0,"
-          " int32_t i1, V* acc, const int32_t* roff) {\n",
+          " int32_t i1, V* acc, const int32_t* roff, int32_t I) {\n",
           cls);
   o += "  const int lane = threadIdx.x & 31;\n  const bool valid = f + lane < f1;\n"
-       "  const int32_t I = a.frows[valid ? f + lane : f];\n  const int32_t ra = a.A.rp[I];\n"
+       "  const int32_t ra = a.A.rp[I];\n"
        "  const int32_t* Aci = a.A.ci + ra;\n  const V* Av = a.A.val + ra;\n  const V* Pv = a.P.val;\n";
   for (int x = 0; x < na; ++x)
     appendf(o, "  const V a%d = Av[%d];\n  const int32_t q%d = a.P.rp[Aci[%d]];\n", x, x, x, x);
@@ -198,9 +242,23 @@ int jit_prepare(ptap_plan* p) {
   for (int32_t o : off) pool_len = std::max(pool_len, o + p->class_maxlen);
   std::vector<uint8_t> pool(pool_len);
   PTAP_CUDA(cudaMemcpy(pool.data(), p->class_pool, pool_len, cudaMemcpyDeviceToHost));
+  // Class ids come from a concurrent deduplication and differ between runs;
+  // the generated source must not, or the disk cache would never hit.  So
+  // classes are ranked by visits with ties broken by program bytes, and the
+  // compiled ones are numbered in program-byte order; a device table maps a
+  // plan's class ids to those numbers.
+  auto prog = [&](int k) { return pool.data() + off[k]; };
+  auto prog_len = [&](int k) {
+    const uint8_t* g = prog(k);
+    return 8 + ((g[0] + 7) & ~7) + 8 * g[0] + 8 * g[1];
+  };
+  auto prog_less = [&](int x, int y) {
+    return std::lexicographical_compare(prog(x), prog(x) + prog_len(x), prog(y), prog(y) + prog_len(y));
+  };
   std::vector<int> order(p->nclasses);
   for (int k = 0; k < p->nclasses; ++k) order[k] = k;
-  std::sort(order.begin(), order.end(), [&](int x, int y) { return visits[x] > visits[y]; });
+  std::sort(order.begin(), order.end(),
+            [&](int x, int y) { return visits[x] != visits[y] ? visits[x] > visits[y] : prog_less(x, y); });
   std::vector<int> hot;
   int64_t covered = 0;
   for (int k : order) {
@@ -209,18 +267,16 @@ int jit_prepare(ptap_plan* p) {
     covered += visits[k];
   }
   if (hot.empty()) return PTAP_ERR_UNSUPPORTED;
-  std::sort(hot.begin(), hot.end());
+  std::sort(hot.begin(), hot.end(), prog_less);
   // source
   std::string src = "#include \"fastkern.cuh\"\nusing namespace ptapk;\n";
   src += p->dtype == PTAP_F64 ? "typedef double V;\n" : "typedef float V;\n";
-  for (int k : hot) src += gen_class(k, pool.data() + off[k]);
+  for (size_t i = 0; i < hot.size(); ++i) src += gen_class((int)i, prog(hot[i]));
   src += "struct Special {\n  __device__ bool operator()(const FastArgs<V>& a, int32_t cls, int32_t f, int32_t f1,"
-         " int32_t i0, int32_t i1, V* acc, const int32_t* roff) const {\n    switch (cls) {\n";
-  for (int k : hot) {
-    char buf[160];
-    snprintf(buf, sizeof buf, "      case %d: cls_%d(a, f, f1, i0, i1, acc, roff); return true;\n", k, k);
-    src += buf;
-  }
+         " int32_t i0, int32_t i1, V* acc, const int32_t* roff, int32_t I) const {\n"
+         "    switch (a.jit_slot[cls]) {\n";
+  for (size_t i = 0; i < hot.size(); ++i)
+    appendf(src, "      case %d: cls_%d(a, f, f1, i0, i1, acc, roff, I); return true;\n", (int)i, (int)i);
   src += "      default: return false;\n    }\n  }\n};\n";
   // 64 registers a thread: 1024 threads of resident CTAs per SM
   appendf(src, "extern \"C\" __global__ void __launch_bounds__(%d, %d) ptap_jit_numeric(FastArgs<V> a) {\n",
@@ -228,18 +284,37 @@ int jit_prepare(ptap_plan* p) {
   src += "  fast_kernel_body<V>(a, Special());\n}\n";
   int dev = 0;
   PTAP_CUDA(cudaGetDevice(&dev));
-  const uint64_t key = fnv64(src) ^ fnv64(kFastKernSource);
+  const char* opts[] = {"--gpu-architecture=sm_103a", "-std=c++17", "-lineinfo"};
+  int rv_major = 0, rv_minor = 0;
+  g_rtc.version(&rv_major, &rv_minor);
+  std::string keytext = src + '\x01' + kFastKernSource + '\x01' + std::to_string(rv_major) + "." +
+                        std::to_string(rv_minor);
+  for (const char* o : opts) keytext += std::string("\x01") + o;
+  const uint64_t key = fnv64(keytext);
   CUfunction fn = nullptr;
   auto it = g_cache.find({dev, key});
   const auto t0 = std::chrono::steady_clock::now();
+  const std::string dir = cache_dir();
+  char fname[64];
+  snprintf(fname, sizeof fname, "jit_%016llx_sm103a.cubin", (unsigned long long)key);
+  std::vector<char> cached;
   if (it != g_cache.end()) {
     fn = it->second;
-  } else {
+  } else if (!dir.empty() && read_file(dir + "/" + fname, cached)) {
+    CUmodule mod = nullptr;
+    if (g_drv.load(&mod, cached.data()) == CUDA_SUCCESS &&
+        g_drv.get_fn(&fn, mod, "ptap_jit_numeric") == CUDA_SUCCESS) {
+      g_cache[{dev, key}] = fn;
+    } else {
+      fn = nullptr;
+      cudaGetLastError();
+    }
+  }
+  if (!fn) {
     nvrtcProgram prog;
     const char* hdr[1] = {kFastKernSource};
     const char* hname[1] = {"fastkern.cuh"};
     if (g_rtc.create(&prog, src.c_str(), "ptap_jit.cu", 1, hdr, hname) != NVRTC_SUCCESS) return PTAP_ERR_CUDA;
-    const char* opts[] = {"--gpu-architecture=sm_103a", "-std=c++17", "-lineinfo"};
     const nvrtcResult rc = g_rtc.compile(prog, 3, opts);
     if (rc != NVRTC_SUCCESS) {
       if (getenv("PTAP_VERBOSE")) {
@@ -261,6 +336,7 @@ int jit_prepare(ptap_plan* p) {
     if (g_drv.load(&mod, cubin.data()) != CUDA_SUCCESS) return PTAP_ERR_CUDA;
     if (g_drv.get_fn(&fn, mod, "ptap_jit_numeric") != CUDA_SUCCESS) return PTAP_ERR_CUDA;
     g_cache[{dev, key}] = fn;
+    if (!dir.empty()) write_file_atomic(dir, fname, cubin);
   }
   // The compiled classes keep their rows of A P in registers, so the
   // interpreted ones use a global scratch instead of shared memory: the
@@ -280,6 +356,13 @@ int jit_prepare(ptap_plan* p) {
   void* rs = nullptr;
   PTAP_TRY(p->mem.get(&rs, (size_t)std::max<int64_t>(ctas, 1) * p->cfg.block_threads *
                                std::max(p->class_maxr, 1) * vb));
+  std::vector<int32_t> slot(p->nclasses, -1);
+  for (size_t i = 0; i < hot.size(); ++i) slot[hot[i]] = (int32_t)i;
+  int32_t* dslot = nullptr;
+  PTAP_TRY(p->mem.get_n(&dslot, p->nclasses));
+  PTAP_CUDA(cudaMemcpyAsync(dslot, slot.data(), slot.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+  PTAP_CUDA(cudaStreamSynchronize(s));
+  p->jit_slot = dslot;
   p->jit_rs = rs;
   p->jit_smem = smem;
   p->jit_fn = (void*)fn;

@@ -342,3 +342,35 @@ def test_specialized_classes(dtype):
         B = oracle.ptap_bound(rounded(A, dtype), rounded(P, dtype)).val
         err = np.abs(C.cpu().numpy().astype(np.float64) - C_i.cpu().numpy().astype(np.float64))
         assert (err <= 2 * tol * B + 1e-300).all()
+
+
+_JIT_PROBE = """
+import sys
+sys.path.insert(0, {root!r})
+import torch
+from paper_1905_08423_gb300 import problems as pb, ptap
+A, P = pb.model_problem(17)
+dA = ptap.Csr.from_host(A, "cuda", torch.float32)
+dP = ptap.Csr.from_host(P, "cuda", torch.float32)
+st = ptap.symbolic(dA, dP, ptap.make_config(specialize=6)).stats()
+print(st["n_specialized"], st["specialize_us"])
+"""
+
+
+def test_specialized_disk_cache(tmp_path):
+    """A second process with the same classes loads the cubin instead of compiling it."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, PTAP_JIT_CACHE=str(tmp_path / "jit"))
+    code = _JIT_PROBE.format(root=root)
+    runs = []
+    for _ in range(2):
+        r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
+                           timeout=600, cwd=root)
+        assert r.returncode == 0, r.stderr[-2000:]
+        runs.append([int(x) for x in r.stdout.split()[-2:]])
+    assert runs[0][0] > 0 and runs[1][0] == runs[0][0]
+    assert len(list((tmp_path / "jit").glob("jit_*_sm103a.cubin"))) == 1
+    assert runs[1][1] < runs[0][1] / 3, runs     # load instead of compile
