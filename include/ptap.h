@@ -160,6 +160,23 @@ int ptap_plan_pattern(const ptap_plan* plan, int32_t* m, int64_t* nnz,
 int ptap_numeric(ptap_plan* plan, const ptap_csr* A, const ptap_csr* P, void* C_val,
                  void* stream);
 
+/* Numeric product from host-resident values (the paper's numeric phase,
+ * Section 3, Eq. 9, repeated as values change, Section 4.1).  A and P give the
+ * device patterns exactly as for ptap_numeric (their `val` fields are
+ * ignored); A_val_host (nnz(A) values), P_val_host (nnz(P) values) and
+ * C_val_host (nnz(C) values, written) are host arrays of the plan's dtype.
+ * The values are staged through two plan-owned sets of device buffers
+ * (allocated on the first call with the plan's allocator; 2 * (nnz(A) +
+ * nnz(P) + nnz(C)) values) on two internal streams: the next call's upload
+ * overlaps this call's product and download.  When `stream` has completed,
+ * C_val_host holds the result.  Page-locked host arrays give asynchronous
+ * copies; pageable ones still work, with copies that block the host.  Calls
+ * on one plan must come from one host thread; the host arrays of a call must
+ * stay valid (inputs unmodified) until `stream` has completed that call.
+ * Errors as ptap_numeric, plus PTAP_ERR_OOM for the staging buffers. */
+int ptap_numeric_host(ptap_plan* plan, const ptap_csr* A, const ptap_csr* P, const void* A_val_host,
+                      const void* P_val_host, void* C_val_host, void* stream);
+
 /* Backward of C = P^T A P (not in the paper).  Given G = dL/dC as nnz(C)
  * values on the plan's pattern, writes dL/dA = (P G P^T) restricted to the
  * pattern of A into dA (nnz(A) values) and dL/dP = (A P G^T + A^T P G)

@@ -90,6 +90,7 @@ int ptap_plan_check(ptap_plan* p, void* stream) {
 void ptap_plan_destroy(ptap_plan* p) {
   if (!p) return;
   cudaStreamSynchronize(p->stream);
+  ptap::host_stage_free(p);
   p->mem.release_all();
   ptap::two_step_free(p);
   delete p;

@@ -160,6 +160,7 @@ struct CsrV {
 // the plan
 // ---------------------------------------------------------------------------
 struct TwoStepData;
+struct HostStage;
 
 }  // namespace ptap
 
@@ -214,6 +215,7 @@ struct ptap_plan {
   int32_t* class_off = nullptr;  // [nclasses] offset of each program in the pool
 
   ptap::TwoStepData* two = nullptr;
+  ptap::HostStage* host = nullptr;  // staging of ptap_numeric_host (host.cu)
 };
 
 struct ptap_batch {
@@ -269,6 +271,9 @@ int build_classes(ptap_plan* p, const ptap_csr* A, const ptap_csr* P, cudaStream
 int prepare_numeric(ptap_plan* p);
 int numeric_owner(ptap_plan* p, const ptap_csr* A, const ptap_csr* P, void* C, cudaStream_t s);
 int numeric_atomic(ptap_plan* p, const ptap_csr* A, const ptap_csr* P, void* C, cudaStream_t s);
+int check_numeric_inputs(const ptap_plan* p, const ptap_csr* A, const ptap_csr* P);
+// host.cu
+void host_stage_free(ptap_plan* p);
 // twostep.cu
 int two_step_numeric(ptap_plan* p, const ptap_csr* A, const ptap_csr* P, void* C, cudaStream_t s);
 void two_step_free(ptap_plan* p);

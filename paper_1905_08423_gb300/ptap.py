@@ -310,6 +310,24 @@ def numeric(plan: Plan, A: Csr, P: Csr, out: torch.Tensor | None = None, stream=
     return out
 
 
+def numeric_host(plan: Plan, A: Csr, P: Csr, A_val: torch.Tensor, P_val: torch.Tensor,
+                 out: torch.Tensor, stream=None):
+    """ptap_numeric_host: C's values from host-resident values of A and P into host ``out``.
+
+    A and P supply the device patterns (their values are not read).  All three
+    value tensors live on the host (pinned for overlapped copies) with the
+    plan's dtype; ``out`` is complete once ``stream`` has been synchronised.
+    """
+    for t, n in ((A_val, A.nnz), (P_val, P.nnz), (out, plan.nnz)):
+        assert t.device.type == "cpu" and t.is_contiguous() and t.numel() == n
+        assert t.dtype == plan.torch_dtype
+    f = _lib().ptap_numeric_host
+    f.argtypes = [_VP, _c.POINTER(_Csr), _c.POINTER(_Csr), _VP, _VP, _VP, _VP]
+    _check(f(plan.handle, _c.byref(A.c()), _c.byref(P.c()), A_val.data_ptr(), P_val.data_ptr(),
+             out.data_ptr(), _stream(stream)), "ptap_numeric_host")
+    return out
+
+
 def backward(plan: Plan, A: Csr, P: Csr, G: torch.Tensor, need_dA=True, need_dP=True,
              stream=None):
     """ptap_backward: (dL/dA on pat(A), dL/dP on pat(P)) given G = dL/dC on pat(C)."""

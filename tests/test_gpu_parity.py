@@ -374,3 +374,32 @@ def test_specialized_disk_cache(tmp_path):
     assert runs[0][0] > 0 and runs[1][0] == runs[0][0]
     assert len(list((tmp_path / "jit").glob("jit_*_sm103a.cubin"))) == 1
     assert runs[1][1] < runs[0][1] / 3, runs     # load instead of compile
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("pinned", [True, False])
+def test_numeric_host(dtype, pinned):
+    """ptap_numeric_host: successive products from host values, each checked against the oracle.
+
+    Three calls in a row (A rescaled before each) overlap through the staging
+    buffers; every host result must match its own inputs.
+    """
+    A, P = pb.model_problem(31)
+    dA_, dP_ = to_dev(A, dtype), to_dev(P, dtype)
+    plan = ptap.symbolic(dA_, dP_)
+    ins, outs = [], []
+    for k in range(3):
+        Ak = pb.rescale_values(A, seed=80 + k)
+        hA = torch.as_tensor(rounded(Ak, dtype).val).to(dtype)
+        hP = torch.as_tensor(rounded(P, dtype).val).to(dtype)
+        hC = torch.full((plan.nnz,), float("nan"), dtype=dtype)
+        if pinned:
+            hA, hP, hC = hA.pin_memory(), hP.pin_memory(), hC.pin_memory()
+        ptap.numeric_host(plan, dA_, dP_, hA, hP, hC)
+        ins.append(Ak)
+        outs.append(hC)
+    torch.cuda.synchronize()
+    Pr = rounded(P, dtype)
+    for Ak, hC in zip(ins, outs):
+        Ar = rounded(Ak, dtype)
+        check_values(hC, oracle.ptap(Ar, Pr).val, oracle.ptap_bound(Ar, Pr).val, dtype)
