@@ -44,6 +44,11 @@ struct SigGeom {
 // Warp-cooperative signature of fine row I into sig[] (shared memory);
 // returns its length, or -1 if the row is outside the fast-path limits.
 // cand/keys: kFastMaxT ints of shared memory each.
+//
+// Rows with at most 32 products stay in registers: the products' columns are
+// sorted with their positions as 64-bit keys by a warp bitonic sort, so each
+// product learns its slot in the sorted row of A P from a ballot.  Longer
+// rows take a shared-memory bitonic sort and binary searches.
 __device__ int compute_sig(const SigGeom& g, int32_t I, uint8_t* sig, int32_t* cand, int32_t* keys,
                            int32_t* status) {
   const int lane = threadIdx.x & 31;
@@ -67,23 +72,53 @@ __device__ int compute_sig(const SigGeom& g, int32_t I, uint8_t* sig, int32_t* c
   off -= pa;
   for (int32_t b = 0; b < pa; ++b) cand[off + b] = g.P.ci[pb + b];
   // zero the whole program region first (padding must be deterministic)
-  for (int x = lane; x < kFastSigCap; x += 32) sig[x] = 0;
+  for (int x = lane; x < kFastSigCap / 4; x += 32) reinterpret_cast<uint32_t*>(sig)[x] = 0u;
   __syncwarp();
-  for (int32_t x = lane; x < T; x += 32) keys[x] = cand[x];
-  __syncwarp();
-  // ascending sort of keys[0, T) (bitonic, comparators all ascending)
-  {
-    int p = 1;
-    while (p < T) p <<= 1;
-    for (int size = 2; size <= p; size <<= 1)
-      for (int j = size >> 1; j > 0; j >>= 1) {
+  int32_t r = 0;
+  const bool small = T <= 32;
+  if (small) {
+    // sort (column, position) pairs; then slots by ranking the first occurrences
+    unsigned long long v = lane < T ? ((unsigned long long)(uint32_t)cand[lane] << 32) | (unsigned)lane : ~0ull;
+#pragma unroll
+    for (int k = 2; k <= 32; k <<= 1)
+#pragma unroll
+      for (int j = k >> 1; j > 0; j >>= 1) {
+        const unsigned long long u = __shfl_xor_sync(0xffffffffu, v, j);
+        const bool keep_min = ((lane & j) == 0) == ((lane & k) == 0);
+        v = keep_min ? (u < v ? u : v) : (u > v ? u : v);
+      }
+    const int32_t key = (int32_t)(v >> 32);
+    const int32_t up = __shfl_up_sync(0xffffffffu, key, 1);
+    const bool first = lane < T && (lane == 0 || up != key);
+    const unsigned m = __ballot_sync(0xffffffffu, first);
+    const unsigned le = lane == 31 ? 0xffffffffu : ((2u << lane) - 1u);
+    const int32_t t = __popc(m & le) - 1;
+    r = __popc(m);
+    __syncwarp();
+    if (first) keys[t] = key;
+    if (lane < T) cand[(int32_t)(v & 0xffffffffu)] = t;  // cand now holds each product's slot
+    __syncwarp();
+  } else {
+    for (int32_t x = lane; x < T; x += 32) keys[x] = cand[x];
+    __syncwarp();
+    // ascending sort of keys[0, T) (bitonic, comparators all ascending;
+    // sizes and strides are powers of two, so shifts and masks index them)
+    int p = 1, lp = 0;
+    while (p < T) {
+      p <<= 1;
+      ++lp;
+    }
+    for (int ls = 1; ls <= lp; ++ls)
+      for (int lj = ls - 1; lj >= 0; --lj) {
+        const int size = 1 << ls, j = 1 << lj;
         for (int t = lane; t < (p >> 1); t += 32) {
+          const int hi = t >> lj, lo = t & (j - 1);
           int x, y;
-          if (j == (size >> 1)) {
-            x = (t / j) * size + (t % j);
-            y = (t / j) * size + size - 1 - (t % j);
+          if (lj == ls - 1) {
+            x = hi * size + lo;
+            y = hi * size + size - 1 - lo;
           } else {
-            x = (t / j) * 2 * j + (t % j);
+            x = (hi << (lj + 1)) + lo;
             y = x + j;
           }
           if (y < T) {
@@ -96,21 +131,21 @@ __device__ int compute_sig(const SigGeom& g, int32_t I, uint8_t* sig, int32_t* c
         }
         __syncwarp();
       }
-  }
-  // unique, in place (each 32-wide window is read before it is written)
-  int32_t r = 0, prev = 0;
-  for (int32_t base = 0; base < T; base += 32) {
-    const int32_t x = base + lane;
-    const int32_t kx = x < T ? keys[x] : 0;
-    int32_t up = __shfl_up_sync(0xffffffffu, kx, 1);
-    if (lane == 0) up = prev;
-    const bool first = x < T && (x == 0 || up != kx);
-    const unsigned m = __ballot_sync(0xffffffffu, first);
-    prev = __shfl_sync(0xffffffffu, kx, 31);
-    __syncwarp();
-    if (first) keys[r + __popc(m & ((1u << lane) - 1u))] = kx;
-    r += __popc(m);
-    __syncwarp();
+    // unique, in place (each 32-wide window is read before it is written)
+    int32_t prev = 0;
+    for (int32_t base = 0; base < T; base += 32) {
+      const int32_t x = base + lane;
+      const int32_t kx = x < T ? keys[x] : 0;
+      int32_t up = __shfl_up_sync(0xffffffffu, kx, 1);
+      if (lane == 0) up = prev;
+      const bool first = x < T && (x == 0 || up != kx);
+      const unsigned m = __ballot_sync(0xffffffffu, first);
+      prev = __shfl_sync(0xffffffffu, kx, 31);
+      __syncwarp();
+      if (first) keys[r + __popc(m & ((1u << lane) - 1u))] = kx;
+      r += __popc(m);
+      __syncwarp();
+    }
   }
   if (r > kFastMaxR) return -1;
   // slot of each of this lane's products (lane = a, up to kFastMaxB of them)
@@ -119,35 +154,47 @@ __device__ int compute_sig(const SigGeom& g, int32_t I, uint8_t* sig, int32_t* c
   if (lane < na) {
     sig[8 + lane] = (uint8_t)pa;
     for (int32_t b = 0; b < pa; ++b) {
-      const int32_t key = cand[off + b];
-      int32_t lo = 0, hi = r;
-      while (lo < hi) {
-        const int32_t mid = (lo + hi) >> 1;
-        if (keys[mid] < key) lo = mid + 1;
-        else hi = mid;
+      int32_t lo;
+      if (small) {
+        lo = cand[off + b];
+      } else {
+        const int32_t key = cand[off + b];
+        int32_t hi = r;
+        lo = 0;
+        while (lo < hi) {
+          const int32_t mid = (lo + hi) >> 1;
+          if (keys[mid] < key) lo = mid + 1;
+          else hi = mid;
+        }
       }
       sig[tsec + lane * 8 + b] = (uint8_t)lo;
     }
   }
   const int ssec = tsec + 8 * na;
   const int tcur = ssec + 8 * r;
-  // positions in the rows of C
-  for (int32_t s = 0; s < pI; ++s) {
+  // positions in the rows of C (sigma): every (s, t) pair searches its C row
+  // in parallel (the rows are short and shared by neighbouring fine rows, so
+  // the searches mostly hit L1)
+  bool too_long = false;
+  for (int32_t e = lane; e < pI * r; e += 32) {
+    const int32_t s = e / r, t = e - s * r;
     const int32_t i = g.P.ci[p0 + s];
     const int32_t c0 = g.C.rp[i], L = g.C.rp[i + 1] - c0;
-    if (L > 255) return -1;
-    if (lane < r) {
-      const int32_t key = keys[lane];
-      int32_t lo = 0, hi = L;
-      while (lo < hi) {
-        const int32_t mid = (lo + hi) >> 1;
-        if (g.C.ci[c0 + mid] < key) lo = mid + 1;
-        else hi = mid;
-      }
-      if (lo >= L || g.C.ci[c0 + lo] != key) atomicExch(status, PTAP_ERR_PATTERN);
-      sig[ssec + lane * 8 + s] = (uint8_t)lo;
+    if (L > 255) {
+      too_long = true;
+      continue;
     }
+    const int32_t kt = keys[t];
+    int32_t lo = 0, hi = L;
+    while (lo < hi) {
+      const int32_t mid = (lo + hi) >> 1;
+      if (g.C.ci[c0 + mid] < kt) lo = mid + 1;
+      else hi = mid;
+    }
+    if (lo >= L || g.C.ci[c0 + lo] != kt) atomicExch(status, PTAP_ERR_PATTERN);
+    sig[ssec + t * 8 + s] = (uint8_t)lo;
   }
+  if (__any_sync(0xffffffffu, too_long)) return -1;
   if (lane == 0) {
     sig[0] = (uint8_t)na;
     sig[1] = (uint8_t)r;
@@ -172,7 +219,8 @@ __device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
 __device__ unsigned long long sig_hash(const uint8_t* sig, int len) {
   const int lane = threadIdx.x & 31;
   unsigned long long h = 0xcbf29ce484222325ull ^ mix64((unsigned long long)(lane + 1) * 0x9e3779b97f4a7c15ull);
-  for (int x = lane; x < len; x += 32) h = (h ^ (unsigned long long)sig[x]) * 0x100000001b3ull;
+  const uint32_t* w = reinterpret_cast<const uint32_t*>(sig);  // len is a multiple of 8
+  for (int x = lane; x < (len >> 2); x += 32) h = (h ^ (unsigned long long)w[x]) * 0x100000001b3ull;
   h = mix64(h + (unsigned long long)lane * 0x632be59bd9b4e019ull + (unsigned long long)len);
 #pragma unroll
   for (int d = 16; d > 0; d >>= 1) h ^= __shfl_xor_sync(0xffffffffu, h, d);
@@ -197,7 +245,7 @@ struct ClassArgs {
 constexpr int kSigWarps = 4;
 
 struct SigSmem {
-  uint8_t sig[kSigWarps][kFastSigCap];
+  __align__(16) uint8_t sig[kSigWarps][kFastSigCap];
   int32_t cand[kSigWarps][kFastMaxT];
   int32_t keys[kSigWarps][kFastMaxT];
 };
@@ -428,7 +476,8 @@ int build_classes(ptap_plan* p, const ptap_csr* A, const ptap_csr* P, cudaStream
   c.counters = counters;
   c.row_class = row_class;
   c.status = p->status;
-  const int grid = num_sms() * 8;
+  // latency-bound warp-per-row work: fill the SMs (16 CTAs of 4 warps each)
+  const int grid = num_sms() * 16;
   k_class_insert<<<grid, kSigWarps * 32, 0, s>>>(c);
   PTAP_LAUNCHED();
   int32_t h[4];
