@@ -82,6 +82,31 @@ __device__ __forceinline__ void red_add(double* p, double v) {
   asm volatile("red.shared.add.f64 [%0], %1;" ::"r"((unsigned)__cvta_generic_to_shared(p)), "d"(v) : "memory");
 }
 
+// *p += w * r for p in shared memory (one outer-product term of Alg. 8).
+// Each form is the one measured fastest where it is used:
+//  - compiled classes: a shared-memory reduction (red.shared.add), FP32 and FP64;
+//  - interpreter, FP32: atomicAdd (fewer registers in its loops);
+//  - interpreter, FP64: a compare-and-swap loop whose new value is
+//    fma(w, r, old) -- one FP64 operation a term on a part whose FP64 pipe
+//    bounds this path (and one rounding).  Lock-free: a failed swap means
+//    another thread's update went in.
+__device__ __forceinline__ void acc_fma(float* p, float w, float r) { red_add(p, w * r); }
+__device__ __forceinline__ void acc_fma(double* p, double w, double r) { red_add(p, w * r); }
+__device__ __forceinline__ void interp_add(float* p, float w, float r) { atomicAdd(p, w * r); }
+__device__ __forceinline__ void interp_add(double* p, double w, double r) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+  unsigned long long old;
+  asm volatile("ld.shared.u64 %0, [%1];" : "=l"(old) : "r"(a) : "memory");
+  for (;;) {
+    const unsigned long long nv =
+        (unsigned long long)__double_as_longlong(fma(w, r, __longlong_as_double((long long)old)));
+    unsigned long long got;
+    asm volatile("atom.shared.cas.b64 %0, [%1], %2, %3;" : "=l"(got) : "r"(a), "l"(old), "l"(nv) : "memory");
+    if (got == old) break;
+    old = got;
+  }
+}
+
 // Interpreter: 32 fine rows [f, min(f+32, f1)) of one class, one per lane.
 // R is the lane's row of A P, lane-major in shared memory (R[t*32 + lane]).
 template <typename V>
@@ -148,7 +173,7 @@ __device__ __forceinline__ void fast_piece(const FastArgs<V>& a, const uint8_t* 
 #pragma unroll
     for (int s = 0; s < kMaxP; ++s) {
       if (s >= pI) break;
-      if (cb[s] >= 0) atomicAdd(&acc[cb[s] + (int)((sw >> (8 * s)) & 0xff)], ws[s] * rt);
+      if (cb[s] >= 0) interp_add(&acc[cb[s] + (int)((sw >> (8 * s)) & 0xff)], ws[s], rt);
     }
   }
 }

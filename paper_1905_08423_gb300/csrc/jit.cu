@@ -212,7 +212,7 @@ std::string gen_class(int cls, const uint8_t* g) {
           "    if (valid && i >= i0 && i < i1) {\n      V* c = acc + roff[i - i0];\n"
           "      const unsigned char* sg = sg_%d + s * %d;\n",
           pI, pI, cls, r);
-  for (int t = 0; t < r; ++t) appendf(o, "      red_add(c + sg[%d], w * R%d);\n", t, t);
+  for (int t = 0; t < r; ++t) appendf(o, "      acc_fma(c + sg[%d], w, R%d);\n", t, t);
   o += "    }\n  }\n}\n";
   return o;
 }
