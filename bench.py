@@ -241,6 +241,45 @@ def bench_batch(ptap, pb, dev, tdt, ev, s, count=64, reps=10, probs=None):
             "graph_replays": reps, "rescale": "A values x U(0.5, 2) per entry between replays"}
 
 
+def bench_cusparse(A, P, dev, tdt, ev, s, reps=3):
+    """Context only: the two-step product C = P^T (A P) as cuSPARSE SpGEMM calls
+    (through torch.sparse), beside this library's own two-step comparator."""
+    import torch
+
+    def csr(M, rows, cols):
+        return torch.sparse_csr_tensor(torch.as_tensor(M.row_ptr, dtype=torch.int64),
+                                       torch.as_tensor(M.col_idx, dtype=torch.int64),
+                                       torch.as_tensor(M.val).to(tdt), size=(rows, cols), device=dev)
+    try:
+        tA = csr(A, A.nrows, A.ncols)
+        tP = csr(P, P.nrows, P.ncols)
+        tPt = tP.t().to_sparse_csr()
+        torch.cuda.synchronize()
+        base = torch.cuda.memory_allocated()
+        torch.cuda.reset_peak_memory_stats()
+        C = tPt @ (tA @ tP)
+        torch.cuda.synchronize()
+        peak = torch.cuda.max_memory_allocated() - base
+        nnz = int(C._nnz())
+        del C
+        a, b = ev(), ev()
+        a.record(s)
+        for _ in range(reps):
+            C = tPt @ (tA @ tP)
+            del C
+        b.record(s)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / reps
+        out = {"ms_per_step": round(ms, 3), "peak_mb": round(peak / 2**20, 1), "nnz_c": nnz,
+               "note": "cuSPARSE SpGEMM via torch.sparse (A P, then P^T (A P)); context, not this library"}
+        del tA, tP, tPt
+        torch.cuda.empty_cache()
+        return out
+    except Exception as e:  # noqa: BLE001 - context only
+        torch.cuda.empty_cache()
+        return {"unavailable": f"{type(e).__name__}: {str(e)[:200]}"}
+
+
 def bench_algebraic(ptap, autotune, pb, dev, ev, s, steps, tuned_ok=True):
     """The irregular algebraic case: 27-point lognormal operator on 200^3, SA 3^3 P, FP64."""
     import torch
@@ -629,6 +668,9 @@ def main():
         plan2.destroy()
         del C2
         torch.cuda.empty_cache()
+
+        # ---- context: the vendor library's two-step SpGEMM on the same input
+        out["cusparse_two_step"] = bench_cusparse(A, P, dev, tdt, ev, s)
 
         # ---- end to end through the C ABI with host buffers (ptap_numeric_host): every
         #      step uploads A's and P's values from pinned memory and downloads C's; the

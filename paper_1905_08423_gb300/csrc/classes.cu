@@ -368,15 +368,18 @@ __global__ void k_chunk_span(const int32_t* __restrict__ fptr, const int32_t* __
 // of one class stay inside a block.  Small blocks make the warps working on a
 // chunk at the same time read neighbouring rows of A and P (L1 reuse); large
 // blocks keep runs long (full warps).  bb is a tuning knob (config).
+// The three visit-list kernels below give each chunk a warp, whose lanes
+// stride over the chunk's visits.
 __global__ void k_visit_keys(const int32_t* __restrict__ fptr, const int32_t* __restrict__ frows,
                              int32_t nch, const int32_t* __restrict__ row_class, int shift,
                              int kBlockBits, int32_t* keys) {
-  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < nch;
-       c += (int64_t)gridDim.x * blockDim.x) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < nch; c += nw) {
     const int32_t f0 = fptr[c], f1 = fptr[c + 1];
     if (f0 == f1) continue;
     const int32_t base = frows[f0];  // lists are ascending before this sort
-    for (int32_t f = f0; f < f1; ++f) {
+    for (int32_t f = f0 + lane; f < f1; f += 32) {
       const int32_t I = frows[f], d = I - base;
       keys[f] = ((d >> kBlockBits) << (shift + kBlockBits)) | (row_class[I] << kBlockBits) |
                 (d & ((1 << kBlockBits) - 1));
@@ -386,10 +389,11 @@ __global__ void k_visit_keys(const int32_t* __restrict__ fptr, const int32_t* __
 
 __global__ void k_seg_flags(const int32_t* __restrict__ fptr, int32_t nch, const int32_t* __restrict__ keys,
                             int shift, int kBlockBits, int32_t* flag) {
-  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < nch;
-       c += (int64_t)gridDim.x * blockDim.x) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < nch; c += nw) {
     const int32_t f0 = fptr[c], f1 = fptr[c + 1];
-    for (int32_t f = f0; f < f1; ++f)
+    for (int32_t f = f0 + lane; f < f1; f += 32)
       flag[f] = (f == f0 || (keys[f] >> kBlockBits) != (keys[f - 1] >> kBlockBits)) ? 1 : 0;
   }
 }
@@ -397,11 +401,12 @@ __global__ void k_seg_flags(const int32_t* __restrict__ fptr, int32_t nch, const
 __global__ void k_seg_fill(const int32_t* __restrict__ fptr, int32_t nch, const int32_t* __restrict__ keys,
                            int shift, int kBlockBits, const int32_t* __restrict__ segid, int32_t* seg_ptr,
                            int32_t* seg_class, int32_t* chunk_seg, int64_t nf) {
-  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < nch;
-       c += (int64_t)gridDim.x * blockDim.x) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < nch; c += nw) {
     const int32_t f0 = fptr[c], f1 = fptr[c + 1];
-    chunk_seg[c] = segid[f0];
-    for (int32_t f = f0; f < f1; ++f)
+    if (lane == 0) chunk_seg[c] = segid[f0];
+    for (int32_t f = f0 + lane; f < f1; f += 32)
       if (f == f0 || (keys[f] >> kBlockBits) != (keys[f - 1] >> kBlockBits)) {
         seg_ptr[segid[f]] = f;
         seg_class[segid[f]] = (keys[f] >> kBlockBits) & ((1 << shift) - 1);
