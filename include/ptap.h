@@ -105,7 +105,11 @@ typedef struct {
   int32_t specialize;     /* k > 0: compile straight-line code (NVRTC, at symbolic time) for
                              at most k classes covering most fine rows; 0 or -1: class
                              programs are interpreted */
-  int32_t reserved[6];
+  int32_t cache_indices;  /* nonzero: the plan also stores, for every entry of A, the first
+                             position of P's row for its column (nnz(A) int32, a cached
+                             intermediate in the sense of Section 4.2), so the class-program
+                             kernels skip one dependent lookup per entry; 0: off */
+  int32_t reserved[5];
 } ptap_config;
 
 /* Statistics of a plan (host struct filled by ptap_plan_stats). */

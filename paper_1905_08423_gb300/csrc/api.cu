@@ -28,6 +28,7 @@ Config resolve_config(const ptap_config* c) {
   r.group_lanes = (g == 4 || g == 8 || g == 16 || g == 32) ? g : r.group_lanes;
   r.ap_slots = std::min(std::max(pick(c->ap_slots, r.ap_slots), 4), 1024);
   r.debug_checks = c->debug_checks != 0;
+  r.cache_indices = c->cache_indices > 0 ? 1 : 0;
   r.force_spill = c->force_spill != 0;
   return r;
 }

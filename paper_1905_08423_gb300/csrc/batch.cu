@@ -99,6 +99,7 @@ static int batch_create_t(ptap_batch* b, ptap_plan* const* plans, const ptap_csr
       f.chunk_order = nullptr;
       f.rs_global = nullptr;
       f.jit_slot = nullptr;
+      f.aq = p->aq;
     }
     NumArgs<V>& a = h[q];
     a.A = CsrV<V>{A[q].nrows, A[q].ncols, A[q].row_ptr, A[q].col_idx, (const V*)A[q].val};

@@ -136,6 +136,7 @@ struct Config {
   int ap_slots = 64;
   int debug_checks = 0;
   int force_spill = 0;
+  int cache_indices = 0;      // store P's row start for every entry of A (fast path)
 };
 
 Config resolve_config(const ptap_config* c);
@@ -207,6 +208,7 @@ struct ptap_plan {
   void* jit_fn = nullptr;
   void* jit_rs = nullptr;  // global scratch for the interpreted classes' rows of A P
   int32_t* jit_slot = nullptr;  // [nclasses] compiled-code number of each class, or -1
+  int32_t* aq = nullptr;        // [nnz(A)] P.rp[A.ci[e]] when indices are cached
   void* interp_rs = nullptr;  // the same for the interpreter kernel, when shared memory is short
   size_t jit_smem = 0;
   int jit_per_sm = 0, jit_classes = 0;
@@ -272,6 +274,8 @@ int prepare_numeric(ptap_plan* p);
 int numeric_owner(ptap_plan* p, const ptap_csr* A, const ptap_csr* P, void* C, cudaStream_t s);
 int numeric_atomic(ptap_plan* p, const ptap_csr* A, const ptap_csr* P, void* C, cudaStream_t s);
 int check_numeric_inputs(const ptap_plan* p, const ptap_csr* A, const ptap_csr* P);
+// fastnum.cu
+int build_index_cache(ptap_plan* p, const ptap_csr* A, const ptap_csr* P, cudaStream_t s);
 // host.cu
 void host_stage_free(ptap_plan* p);
 // twostep.cu

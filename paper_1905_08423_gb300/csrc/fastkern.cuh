@@ -69,6 +69,9 @@ struct FastArgs {
   // Plan-time specialised code: the compiled-code number of each class, or
   // -1 (null without compiled code).
   const int32_t* jit_slot;
+  // Optional cached index: aq[e] = P.rp[A.ci[e]] for every entry e of A
+  // (null: looked up through A.ci).
+  const int32_t* aq;
 };
 
 // Adds v to *p, p in shared memory.  A relaxed reduction: the barrier that
@@ -124,18 +127,18 @@ __device__ __forceinline__ void fast_piece(const FastArgs<V>& a, const uint8_t* 
   // row of A P (Alg. 3), four entries of A(I,:) at a time
   const int32_t ra = a.A.rp[I];
   for (int x0 = 0; x0 < na; x0 += 4) {
-    int32_t k[4];
+    int32_t k[4] = {0, 0, 0, 0};
     V av[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j)
       if (x0 + j < na) {
-        k[j] = a.A.ci[ra + x0 + j];
+        if (!a.aq) k[j] = a.A.ci[ra + x0 + j];
         av[j] = a.A.val[ra + x0 + j];
       }
     int32_t pb[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j)
-      if (x0 + j < na) pb[j] = a.P.rp[k[j]];
+      if (x0 + j < na) pb[j] = a.aq ? a.aq[ra + x0 + j] : a.P.rp[k[j]];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       if (x0 + j >= na) break;

@@ -53,6 +53,7 @@ static FastArgs<V> fast_args(ptap_plan* p, const ptap_csr* A, const ptap_csr* P,
   a.chunk_order = p->chunk_order;
   a.rs_global = (V*)p->interp_rs;
   a.jit_slot = p->jit_slot;
+  a.aq = p->aq;
   return a;
 }
 
@@ -126,6 +127,21 @@ static int prepare_fast_t(ptap_plan* p) {
   }
   p->num_smem = smem;
   p->num_per_sm = per_sm;
+  return PTAP_OK;
+}
+
+// The cached index of the class-program kernels: aq[e] = P.rp[A.ci[e]].
+__global__ void k_index_cache(const int32_t* __restrict__ Aci, const int32_t* __restrict__ Prp, int64_t nnz,
+                              int32_t* __restrict__ aq) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x)
+    aq[e] = Prp[Aci[e]];
+}
+
+int build_index_cache(ptap_plan* p, const ptap_csr* A, const ptap_csr* P, cudaStream_t s) {
+  if (!p->fast || !p->cfg.cache_indices || p->aq || p->nnz_a == 0) return PTAP_OK;
+  PTAP_TRY(p->mem.get_n(&p->aq, p->nnz_a));
+  k_index_cache<<<num_sms() * 8, 256, 0, s>>>(A->col_idx, P->row_ptr, p->nnz_a, p->aq);
+  PTAP_LAUNCHED();
   return PTAP_OK;
 }
 

@@ -177,7 +177,7 @@ void appendf(std::string& o, const char* fmt, ...) {
 // at offsets sigma(s, t) read from a per-class constant table (Alg. 8).  The
 // loop keeps the code of a class near r accumulations instead of r * pI: the
 // instruction cache, not the issue rate, limits how many classes pay off.
-std::string gen_class(int cls, const uint8_t* g) {
+std::string gen_class(int cls, const uint8_t* g, bool cached) {
   const int na = g[0], r = g[1], pI = g[2];
   const uint8_t* pa = g + 8;
   const uint8_t* tsec = g + 8 + ((na + 7) & ~7);
@@ -194,8 +194,13 @@ std::string gen_class(int cls, const uint8_t* g) {
   o += "  const int lane = threadIdx.x & 31;\n  const bool valid = f + lane < f1;\n"
        "  const int32_t ra = a.A.rp[I];\n"
        "  const int32_t* Aci = a.A.ci + ra;\n  const V* Av = a.A.val + ra;\n  const V* Pv = a.P.val;\n";
-  for (int x = 0; x < na; ++x)
-    appendf(o, "  const V a%d = Av[%d];\n  const int32_t q%d = a.P.rp[Aci[%d]];\n", x, x, x, x);
+  if (cached) o += "  const int32_t* Aq = a.aq + ra;\n  (void)Aci;\n";
+  for (int x = 0; x < na; ++x) {
+    if (cached)
+      appendf(o, "  const V a%d = Av[%d];\n  const int32_t q%d = Aq[%d];\n", x, x, x, x);
+    else
+      appendf(o, "  const V a%d = Av[%d];\n  const int32_t q%d = a.P.rp[Aci[%d]];\n", x, x, x, x);
+  }
   // slots of the row of A P, products summed in the interpreter's (a, b) order
   for (int t = 0; t < r; ++t) {
     appendf(o, "  V R%d = V(0);\n", t);
@@ -271,7 +276,7 @@ int jit_prepare(ptap_plan* p) {
   // source
   std::string src = "#include \"fastkern.cuh\"\nusing namespace ptapk;\n";
   src += p->dtype == PTAP_F64 ? "typedef double V;\n" : "typedef float V;\n";
-  for (size_t i = 0; i < hot.size(); ++i) src += gen_class((int)i, prog(hot[i]));
+  for (size_t i = 0; i < hot.size(); ++i) src += gen_class((int)i, prog(hot[i]), p->aq != nullptr);
   src += "struct Special {\n  __device__ bool operator()(const FastArgs<V>& a, int32_t cls, int32_t f, int32_t f1,"
          " int32_t i0, int32_t i1, V* acc, const int32_t* roff, int32_t I) const {\n"
          "    switch (a.jit_slot[cls]) {\n";

@@ -778,6 +778,7 @@ static int symbolic_body(ptap_plan* p, const ptap_csr* A, const ptap_csr* P) {
     }
   }
   if (!p->fast) p->cfg.block_threads = std::min(p->cfg.block_threads, 256);
+  PTAP_TRY(build_index_cache(p, A, P, s));
   PTAP_TRY(prepare_numeric(p));
   PTAP_CUDA(cudaStreamSynchronize(s));
   int32_t st = 0;

@@ -69,6 +69,8 @@ CONFIGS = [
     dict(specialize=4, chunk_entries=1024),       # compiled classes and interpreted ones mixed
     dict(block_threads=1024, chunk_entries=32768),  # interpreter, rows of A P in global scratch
     dict(block_threads=512, class_programs=False),  # general kernel: CTA clamped to 256
+    dict(cache_indices=True),                     # cached P row starts, interpreter
+    dict(cache_indices=True, specialize=4, chunk_entries=1024),  # ... and compiled classes
 ]
 
 
@@ -77,6 +79,7 @@ LARGE_CTA = [
     dict(specialize=4, block_threads=1024, chunk_entries=32768),
     dict(block_threads=1024, chunk_entries=32768),
     dict(block_threads=512, chunk_entries=12288),
+    dict(specialize=8, block_threads=1024, chunk_entries=32768, cache_indices=True),
 ]
 
 
