@@ -599,7 +599,7 @@ def main():
         cfg_kw = {}
     else:
         # launch parameters picked by timing candidates on this problem (not timed below)
-        tuned = autotune.tune(dA, dP, reps=3, warmup=2, cache_path=None, use_cache=False)
+        tuned = autotune.tune(dA, dP, reps=10, warmup=3, cache_path=None, use_cache=False)
         cfg_kw = dict(tuned.config)
     cfg = ptap.make_config(**cfg_kw)
 

@@ -5,8 +5,7 @@ The numeric product is repeated many times on one symbolic result (Section
 products to pick the launch parameters pay for themselves.  ``tune`` builds a
 plan per candidate configuration (chunk size of the on-chip accumulator, CTA
 size, lanes per fine row and hash slots of the general kernel, visit order and
-plan-time specialisation of the class-program kernel, whether the plan caches
-P's row starts per entry of A (more memory, less time), owner or atomic scheme),
+plan-time specialisation of the class-program kernel, owner or atomic scheme),
 times repeated numeric products with CUDA events, and returns the fastest.
 Choices are cached in a JSON file keyed by (GPU name, dtype, problem
 signature); the signature is the shapes, the nonzero counts and a hash of the
@@ -31,8 +30,7 @@ CANDIDATES = [
     dict(specialize=8, block_threads=1024, chunk_entries=32768),
     dict(specialize=16, block_threads=1024, chunk_entries=32768),
     dict(specialize=32, block_threads=1024, chunk_entries=32768),
-    dict(specialize=32, block_threads=1024, chunk_entries=32768, cache_indices=True),
-    dict(specialize=16, block_threads=1024, chunk_entries=32768, cache_indices=True),
+
     dict(specialize=4, block_threads=1024, chunk_entries=32768),
     dict(block_threads=512, chunk_entries=16384),
     dict(chunk_entries=4096),
