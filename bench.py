@@ -314,7 +314,8 @@ def bench_algebraic(ptap, autotune, pb, dev, ev, s, steps, tuned_ok=True):
     A, P = pb.algebraic_problem(200, seed=3)
     dA = ptap.Csr.from_host(A, dev, torch.float64)
     dP = ptap.Csr.from_host(P, dev, torch.float64)
-    cands = [dict(), dict(specialize=8), dict(specialize=8, block_threads=512, chunk_entries=16384),
+    cands = [dict(), dict(specialize=8, block_threads=512, chunk_entries=16384),
+             dict(specialize=32, block_threads=512, chunk_entries=16384),
              dict(block_threads=1024, chunk_entries=24576), dict(class_programs=False)]
     t = (autotune.tune(dA, dP, candidates=cands, reps=3, warmup=2, cache_path=None, use_cache=False)
          if tuned_ok else None)
@@ -850,8 +851,10 @@ def main():
         if args.dtype == "f32":
             d64A = ptap.Csr.from_host(A, dev, torch.float64)
             d64P = ptap.Csr.from_host(P, dev, torch.float64)
-            cands = [dict(), dict(specialize=8), dict(specialize=8, block_threads=512, chunk_entries=16384),
-                     dict(specialize=8, block_threads=1024, chunk_entries=24576)]
+            cands = [dict(), dict(specialize=8, block_threads=512, chunk_entries=16384),
+                     dict(specialize=16, block_threads=512, chunk_entries=16384),
+                     dict(specialize=32, block_threads=512, chunk_entries=16384),
+                     dict(specialize=32, block_threads=1024, chunk_entries=24576)]
             t64 = autotune.tune(d64A, d64P, candidates=cands, reps=3, warmup=2, cache_path=None,
                                 use_cache=False) if tuned else None
             plan64 = ptap.symbolic(d64A, d64P, ptap.make_config(**(t64.config if t64 else {})))

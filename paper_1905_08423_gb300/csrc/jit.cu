@@ -283,9 +283,12 @@ int jit_prepare(ptap_plan* p) {
   for (size_t i = 0; i < hot.size(); ++i)
     appendf(src, "      case %d: cls_%d(a, f, f1, i0, i1, acc, roff, I); return true;\n", (int)i, (int)i);
   src += "      default: return false;\n    }\n  }\n};\n";
-  // 64 registers a thread: 1024 threads of resident CTAs per SM
+  // FP32: 64 registers a thread, 1024 resident threads per SM.  FP64 code
+  // holds twice the bytes in registers and spills at 64; 128 registers with
+  // 512 resident threads measured faster.
+  const int resident = p->dtype == PTAP_F64 ? 512 : 1024;
   appendf(src, "extern \"C\" __global__ void __launch_bounds__(%d, %d) ptap_jit_numeric(FastArgs<V> a) {\n",
-          p->cfg.block_threads, std::max(1, 1024 / p->cfg.block_threads));
+          p->cfg.block_threads, std::max(1, resident / p->cfg.block_threads));
   src += "  fast_kernel_body<V>(a, Special());\n}\n";
   int dev = 0;
   PTAP_CUDA(cudaGetDevice(&dev));
