@@ -109,7 +109,10 @@ typedef struct {
                              position of P's row for its column (nnz(A) int32, a cached
                              intermediate in the sense of Section 4.2), so the class-program
                              kernels skip one dependent lookup per entry; 0: off */
-  int32_t reserved[5];
+  int32_t general_kernel; /* general owner-mode kernel (rows outside the class programs):
+                             0 = sort-based, one warp per fine row (default);
+                             1 = hash tables per group of group_lanes lanes */
+  int32_t reserved[4];
 } ptap_config;
 
 /* Statistics of a plan (host struct filled by ptap_plan_stats). */

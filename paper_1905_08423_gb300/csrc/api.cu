@@ -29,6 +29,7 @@ Config resolve_config(const ptap_config* c) {
   r.ap_slots = std::min(std::max(pick(c->ap_slots, r.ap_slots), 4), 1024);
   r.debug_checks = c->debug_checks != 0;
   r.cache_indices = c->cache_indices > 0 ? 1 : 0;
+  r.general_kernel = c->general_kernel == 1 ? 1 : 0;
   r.force_spill = c->force_spill != 0;
   return r;
 }

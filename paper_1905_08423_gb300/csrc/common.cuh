@@ -137,6 +137,7 @@ struct Config {
   int debug_checks = 0;
   int force_spill = 0;
   int cache_indices = 0;      // store P's row start for every entry of A (fast path)
+  int general_kernel = 0;     // general path: 0 sort-based (warp per row), 1 hash groups
 };
 
 Config resolve_config(const ptap_config* c);

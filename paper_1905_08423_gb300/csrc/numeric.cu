@@ -217,16 +217,27 @@ static int launch_atomic_g(ptap_plan* p, const NumArgs<V>& a, cudaStream_t s) {
 
 int prepare_fast(ptap_plan* p);
 int numeric_fast(ptap_plan* p, const ptap_csr* A, const ptap_csr* P, void* C, cudaStream_t s);
+int prepare_sorted(ptap_plan* p);  // sorted.cu
+template <typename V>
+int launch_sorted_t(ptap_plan* p, const NumArgs<V>& a, cudaStream_t s);
+
+// The general owner-mode kernel: sort-based unless the hash groups were asked
+// for, or tiny tables are forced (which exercises the hash path's spills).
+static bool use_sorted(const ptap_plan* p) { return p->cfg.general_kernel == 0 && !p->cfg.force_spill; }
 
 int prepare_numeric(ptap_plan* p) {
   if (p->cfg.mode == PTAP_MODE_ATOMIC) PTAP_DISPATCH_VG(p, (prepare_atomic_g<V, G>(p)));
   if (p->fast) return prepare_fast(p);
+  if (use_sorted(p)) return prepare_sorted(p);
   PTAP_DISPATCH_VG(p, (prepare_owner_g<V, G>(p)));
 }
 
 int numeric_owner(ptap_plan* p, const ptap_csr* A, const ptap_csr* P, void* C, cudaStream_t s) {
   if (p->nchunks == 0) return PTAP_OK;
   if (p->fast) return numeric_fast(p, A, P, C, s);
+  if (use_sorted(p))
+    return p->dtype == PTAP_F64 ? launch_sorted_t<double>(p, make_args<double>(p, A, P, C), s)
+                                : launch_sorted_t<float>(p, make_args<float>(p, A, P, C), s);
   PTAP_DISPATCH_VG(p, (launch_owner_g<V, G>(p, make_args<V>(p, A, P, C), s)));
 }
 

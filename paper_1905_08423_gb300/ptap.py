@@ -55,7 +55,8 @@ class _Config(_c.Structure):
                 ("ap_slots", _c.c_int32), ("debug_checks", _c.c_int32),
                 ("force_spill", _c.c_int32), ("class_programs", _c.c_int32),
                 ("visit_block_log2", _c.c_int32), ("specialize", _c.c_int32),
-                ("cache_indices", _c.c_int32), ("reserved", _c.c_int32 * 5)]
+                ("cache_indices", _c.c_int32), ("general_kernel", _c.c_int32),
+                ("reserved", _c.c_int32 * 4)]
 
 
 class _Stats(_c.Structure):
@@ -201,7 +202,7 @@ class Csr:
 
 def make_config(mode=MODE_OWNER, chunk_entries=0, block_threads=0, group_lanes=0, ap_slots=0,
                 debug_checks=False, force_spill=False, class_programs=True,
-                visit_block_log2=0, specialize=False, cache_indices=False) -> _Config:
+                visit_block_log2=0, specialize=False, cache_indices=False, general_kernel=0) -> _Config:
     cfg = _Config()
     cfg.mode = mode
     cfg.chunk_entries = chunk_entries
@@ -214,6 +215,7 @@ def make_config(mode=MODE_OWNER, chunk_entries=0, block_threads=0, group_lanes=0
     cfg.visit_block_log2 = visit_block_log2
     cfg.specialize = 8 if specialize is True else (-1 if not specialize else int(specialize))
     cfg.cache_indices = int(bool(cache_indices))
+    cfg.general_kernel = int(general_kernel)
     return cfg
 
 

@@ -69,6 +69,9 @@ CONFIGS = [
     dict(specialize=4, chunk_entries=1024),       # compiled classes and interpreted ones mixed
     dict(block_threads=1024, chunk_entries=32768),  # interpreter, rows of A P in global scratch
     dict(block_threads=512, class_programs=False),  # general kernel: CTA clamped to 256
+    dict(class_programs=False, general_kernel=1),  # general kernel with hash groups
+    dict(class_programs=False, chunk_entries=128),  # sort-based general kernel, heavy chunks
+    dict(class_programs=False, block_threads=64),  # sort-based general kernel, 2 warps a CTA
     dict(cache_indices=True),                     # cached P row starts, interpreter
     dict(cache_indices=True, specialize=4, chunk_entries=1024),  # ... and compiled classes
 ]
