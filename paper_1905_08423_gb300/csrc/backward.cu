@@ -154,6 +154,7 @@ int check_numeric_inputs(const ptap_plan* p, const ptap_csr* A, const ptap_csr* 
 
 extern "C" int ptap_backward(ptap_plan* p, const ptap_csr* A, const ptap_csr* P, const void* G,
                              void* dA, void* dP, void* stream) {
+  ptap::Range range("ptap_backward");
   if (!p) return PTAP_ERR_INVALID;
   PTAP_TRY(ptap::check_numeric_inputs(p, A, P));
   if (p->nnz_c > 0 && !G) return PTAP_ERR_INVALID;

@@ -287,6 +287,7 @@ extern "C" int ptap_batch_create(ptap_plan* const* plans, const ptap_csr* A, con
 }
 
 extern "C" int ptap_batch_numeric(ptap_batch* b, void* stream) {
+  ptap::Range range("ptap_batch_numeric");
   if (!b) return PTAP_ERR_INVALID;
   if (b->total_items == 0) return PTAP_OK;
   return ptap::batch_launch(b, (cudaStream_t)stream);

@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include <cstdio>
@@ -13,6 +14,15 @@
 #include "ptap.h"
 
 namespace ptap {
+
+// Named range for profilers (NVTX): a timeline shows the library's phases.
+// It costs nothing unless a profiling tool is attached.
+struct Range {
+  explicit Range(const char* name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+  Range(const Range&) = delete;
+  Range& operator=(const Range&) = delete;
+};
 
 // ---------------------------------------------------------------------------
 // error handling: no exception crosses the ABI; internal code returns codes.

@@ -75,6 +75,7 @@ extern "C" int ptap_numeric(ptap_plan* p, const ptap_csr* A, const ptap_csr* P, 
 
 extern "C" int ptap_numeric_host(ptap_plan* p, const ptap_csr* A, const ptap_csr* P, const void* A_val_host,
                                  const void* P_val_host, void* C_val_host, void* stream) {
+  ptap::Range range("ptap_numeric_host");
   if (!p || !A || !P) return PTAP_ERR_INVALID;
   if ((p->nnz_a > 0 && !A_val_host) || (p->nnz_p > 0 && !P_val_host) || (p->nnz_c > 0 && !C_val_host))
     return PTAP_ERR_INVALID;

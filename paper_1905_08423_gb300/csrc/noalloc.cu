@@ -145,6 +145,7 @@ int launch(ptap_plan* const* plans, const ptap_csr* A, const ptap_csr* P, void* 
 extern "C" int ptap_batch_numeric_noalloc(ptap_plan* const* plans, const ptap_csr* A,
                                           const ptap_csr* P, void* const* C_vals, int32_t count,
                                           void* stream) {
+  ptap::Range range("ptap_batch_numeric_noalloc");
   using namespace ptap;
   if (!plans || !A || !P || !C_vals || count <= 0) return PTAP_ERR_INVALID;
   if (count > PTAP_NOALLOC_MAX_PROBLEMS) return PTAP_ERR_OVERFLOW;

@@ -268,6 +268,7 @@ int check_numeric_inputs(const ptap_plan* p, const ptap_csr* A, const ptap_csr* 
 
 extern "C" int ptap_numeric(ptap_plan* p, const ptap_csr* A, const ptap_csr* P, void* C_val,
                             void* stream) {
+  ptap::Range range("ptap_numeric");
   if (!p) return PTAP_ERR_INVALID;
   PTAP_TRY(ptap::check_numeric_inputs(p, A, P));
   if (p->nnz_c > 0 && !C_val) return PTAP_ERR_INVALID;

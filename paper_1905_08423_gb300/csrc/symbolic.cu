@@ -745,6 +745,7 @@ static int symbolic_body(ptap_plan* p, const ptap_csr* A, const ptap_csr* P) {
     PTAP_TRY(transpose_pattern(p->mem, Pi, tp, tj, nullptr, s));
     Expand3 ex{CsrI{m, P->nrows, tp, tj}, CsrI{A->nrows, A->ncols, A->row_ptr, A->col_idx}, Pi};
     int spilled = 0;
+    Range range("ptap: pattern of C");
     PTAP_TRY(union_pattern(p->mem, ex, m, m, p->cfg, p->c_rp, &p->c_ci, &p->nnz_c, p->status,
                            &spilled, s));
     p->spill_rows = spilled;
@@ -764,8 +765,12 @@ static int symbolic_body(ptap_plan* p, const ptap_csr* A, const ptap_csr* P) {
   const int user_value = p->cfg.chunk_entries;
   p->cfg.chunk_entries = user_ch ? std::min(user_value, try_fast ? ch_fast_max : ch_general_max)
                                  : (try_fast ? ch_fast : ch_general);
-  PTAP_TRY(build_schedule(p, P, s));
+  {
+    Range range("ptap: chunk schedule");
+    PTAP_TRY(build_schedule(p, P, s));
+  }
   if (try_fast) {
+    Range range("ptap: structure classes");
     PTAP_TRY(build_classes(p, A, P, s));
     const int general_ch = user_ch ? std::min(user_value, ch_general_max) : ch_general;
     if (!p->fast && p->cfg.chunk_entries != general_ch) {
@@ -779,7 +784,10 @@ static int symbolic_body(ptap_plan* p, const ptap_csr* A, const ptap_csr* P) {
   }
   if (!p->fast) p->cfg.block_threads = std::min(p->cfg.block_threads, 256);
   PTAP_TRY(build_index_cache(p, A, P, s));
-  PTAP_TRY(prepare_numeric(p));
+  {
+    Range range("ptap: prepare numeric (code generation)");
+    PTAP_TRY(prepare_numeric(p));
+  }
   PTAP_CUDA(cudaStreamSynchronize(s));
   int32_t st = 0;
   PTAP_CUDA(cudaMemcpy(&st, p->status, sizeof(int32_t), cudaMemcpyDeviceToHost));
@@ -792,6 +800,7 @@ static int symbolic_body(ptap_plan* p, const ptap_csr* A, const ptap_csr* P) {
 
 extern "C" int ptap_symbolic(const ptap_csr* A, const ptap_csr* P, const ptap_config* cfg,
                              const ptap_allocator* alloc, void* stream, ptap_plan** out) {
+  ptap::Range range("ptap_symbolic");
   ptap_plan* p = nullptr;
   PTAP_TRY(ptap::symbolic_prologue(A, P, cfg, alloc, stream, &p, 0));
   int rc = ptap::symbolic_body(p, A, P);

@@ -206,6 +206,7 @@ static int two_step_body(ptap_plan* p, const ptap_csr* A, const ptap_csr* P) {
 
 extern "C" int ptap_two_step_symbolic(const ptap_csr* A, const ptap_csr* P, const ptap_config* cfg,
                                       const ptap_allocator* alloc, void* stream, ptap_plan** out) {
+  ptap::Range range("ptap_two_step_symbolic");
   ptap_plan* p = nullptr;
   PTAP_TRY(ptap::symbolic_prologue(A, P, cfg, alloc, stream, &p, 1));
   int rc = ptap::two_step_body(p, A, P);
