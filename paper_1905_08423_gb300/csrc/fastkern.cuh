@@ -75,9 +75,7 @@ struct FastArgs {
 };
 
 // Adds v to *p, p in shared memory.  A relaxed reduction: the barrier that
-// ends the chunk orders it before the accumulator is read.  (The generated
-// code uses it; the interpreter keeps atomicAdd, which needs fewer registers
-// in its loops.)
+// ends the chunk orders it before the accumulator is read.
 __device__ __forceinline__ void red_add(float* p, float v) {
   asm volatile("red.shared.add.f32 [%0], %1;" ::"r"((unsigned)__cvta_generic_to_shared(p)), "f"(v) : "memory");
 }
@@ -277,7 +275,8 @@ __device__ __forceinline__ void fast_chunk(const FastArgs<V>& a, int32_t c, Fast
   __syncthreads();
 }
 
-// The single-product kernel body: chunks strided over the grid.
+// The single-product kernel body: chunks from a counter, longest first (or,
+// without the plan's counter, strided over the grid).
 template <typename V, typename Special>
 __device__ __forceinline__ void fast_kernel_body(const FastArgs<V>& a, Special special) {
   extern __shared__ __align__(16) unsigned char smraw[];
