@@ -23,10 +23,12 @@
 // fall back to the general kernel.
 //
 // Deduplication: a 64-bit hash of each signature goes into an open-addressing
-// table (atomicCAS); the smallest fine row with each hash writes its signature
-// to the program pool; then every row compares its own signature byte by byte
-// with the pool entry of its hash, so a hash collision can only demote rows to
-// the general path, never corrupt results.  No kernel waits on another.
+// table (atomicCAS); the row that inserts a hash writes its signature to the
+// program pool and flags it ready; every other row compares its own signature
+// byte by byte with the pool entry of its hash -- at once when the entry is
+// ready, otherwise in a short second pass -- so a hash collision can only
+// demote rows to the general path, never corrupt results.  No warp waits on
+// another.
 #include <algorithm>
 #include <vector>
 
@@ -232,14 +234,16 @@ struct ClassArgs {
   SigGeom g;
   int32_t n;
   unsigned long long* tkey;  // table keys (hash), kEmptyKey = free
-  int32_t* trep;             // smallest fine row per key
+  int32_t* tready;           // per slot: 1 once the key's program is in the pool
   int32_t* tcls;             // class id per slot
   int tlog2;
   uint8_t* pool;
   int64_t pool_cap;
   int32_t* class_off;        // [K+1] pool offset per class (class_off[k] = start)
-  int32_t* counters;         // [0] classes, [1] pool bytes used, [2] slow rows, [3] overflow
-  int32_t* row_class;        // per fine row: class id, or -1 (no P entries), or -2 (general path)
+  int32_t* counters;         // [0] classes, [1] pool bytes used, [2] slow rows, [3] overflow,
+                             // [4] rows left to verify
+  int32_t* row_class;        // per fine row: class id, or -1 (no P entries), or -2 (general
+                             // path), or -3 (to be verified by k_class_verify)
   int32_t* status;
 };
 
@@ -251,76 +255,117 @@ struct SigSmem {
   int32_t keys[kSigWarps][kFastMaxT];
 };
 
-// Phase 1: hash every row's signature into the table.
-__global__ void __launch_bounds__(kSigWarps * 32) k_class_insert(ClassArgs c) {
+// Byte-compares the warp's signature sig[0, len) with the pool entry of class
+// cls; reads bypass L1 (entries may have been written by another SM during
+// this launch).
+__device__ bool same_program(const ClassArgs& c, int32_t cls, const uint8_t* sig, int len) {
+  const int lane = threadIdx.x & 31;
+  const uint8_t* ref = c.pool + __ldcg(&c.class_off[cls]);
+  const int rlen = 8 + ((__ldcg(ref) + 7) & ~7) + 8 * __ldcg(ref) + 8 * __ldcg(ref + 1);
+  bool same = rlen == len;
+  if (same)
+    for (int x = lane; x < len; x += 32) same &= (__ldcg(ref + x) == sig[x]);
+  return __all_sync(0xffffffffu, same);
+}
+
+// One pass over the fine rows: each row's signature is hashed into the table.
+// The row that inserts a key publishes its program to the pool and then sets
+// the slot's ready flag; a row that finds its key already ready compares its
+// signature with the published bytes at once.  A row whose key is not yet
+// ready (its publisher is still writing, on another SM) is marked -3 and
+// checked by k_class_verify after this launch.  Nothing waits on another
+// warp; a 64-bit hash collision can only send rows to the general path.
+__global__ void __launch_bounds__(kSigWarps * 32) k_class_build(ClassArgs c) {
   __shared__ SigSmem sm;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t mask = (1u << c.tlog2) - 1u;
   for (int64_t I = (int64_t)blockIdx.x * kSigWarps + w; I < c.n; I += (int64_t)gridDim.x * kSigWarps) {
-    if (c.g.P.rp[I + 1] == c.g.P.rp[I]) continue;  // never visited
+    if (c.g.P.rp[I + 1] == c.g.P.rp[I]) {  // never visited
+      if (lane == 0) c.row_class[I] = -1;
+      continue;
+    }
     const int len = compute_sig(c.g, (int32_t)I, sm.sig[w], sm.cand[w], sm.keys[w], c.status);
     if (len < 0) {
-      if (lane == 0) atomicAdd(&c.counters[2], 1);
+      if (lane == 0) {
+        c.row_class[I] = -2;
+        atomicAdd(&c.counters[2], 1);
+      }
       continue;
     }
     const unsigned long long h = sig_hash(sm.sig[w], len);
+    int role = 0;  // 1: this row publishes the key, 2: the key exists, 0: table full
+    uint32_t slot = (uint32_t)(h >> 20) & mask;
     if (lane == 0) {
-      uint32_t slot = (uint32_t)(h >> 20) & mask;
-      bool done = false;
       for (uint32_t probe = 0; probe <= mask; ++probe) {
-        const unsigned long long old = atomicCAS(&c.tkey[slot], kEmptyKey, h);
-        if (old == kEmptyKey || old == h) {
-          atomicMin(&c.trep[slot], (int32_t)I);
-          done = true;
+        unsigned long long old = *(volatile unsigned long long*)&c.tkey[slot];
+        if (old == kEmptyKey) old = atomicCAS(&c.tkey[slot], kEmptyKey, h);
+        if (old == kEmptyKey) {
+          role = 1;
+          break;
+        }
+        if (old == h) {
+          role = 2;
           break;
         }
         slot = (slot + 1) & mask;
       }
-      if (!done) atomicExch(&c.counters[3], 1);
+      if (role == 0) atomicExch(&c.counters[3], 1);
     }
-    __syncwarp();
-  }
-}
-
-// Phase 2: the representative of every occupied slot writes the pool entry.
-__global__ void __launch_bounds__(kSigWarps * 32) k_class_publish(ClassArgs c) {
-  __shared__ SigSmem sm;
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t cap = (int64_t)1 << c.tlog2;
-  for (int64_t slot = (int64_t)blockIdx.x * kSigWarps + w; slot < cap;
-       slot += (int64_t)gridDim.x * kSigWarps) {
-    if (c.tkey[slot] == kEmptyKey) continue;
-    const int32_t I = c.trep[slot];
-    const int len = compute_sig(c.g, I, sm.sig[w], sm.cand[w], sm.keys[w], c.status);
-    int32_t cls = -1, off = 0;
-    if (lane == 0 && len > 0) {
-      off = atomicAdd(&c.counters[1], len);
-      if ((int64_t)off + len <= c.pool_cap) {
-        cls = atomicAdd(&c.counters[0], 1);
-        c.class_off[cls] = off;
-      } else {
-        atomicExch(&c.counters[3], 1);
+    role = __shfl_sync(0xffffffffu, role, 0);
+    slot = __shfl_sync(0xffffffffu, slot, 0);
+    int32_t cls = -2;
+    if (role == 1) {
+      int32_t off = 0;
+      if (lane == 0) {
+        off = atomicAdd(&c.counters[1], len);
+        if ((int64_t)off + len <= c.pool_cap) {
+          cls = atomicAdd(&c.counters[0], 1);
+          c.class_off[cls] = off;
+        } else {
+          cls = -1;
+          atomicExch(&c.counters[3], 1);
+        }
       }
-      c.tcls[slot] = cls;
+      cls = __shfl_sync(0xffffffffu, cls, 0);
+      off = __shfl_sync(0xffffffffu, off, 0);
+      if (cls >= 0)
+        for (int x = lane; x < len; x += 32) c.pool[off + x] = sm.sig[w][x];
+      __syncwarp();
+      if (lane == 0) {
+        c.tcls[slot] = cls;
+        __threadfence();  // the program and its class id before the flag
+        atomicExch(&c.tready[slot], 1);
+      }
+      if (cls < 0) cls = -2;
+    } else if (role == 2) {
+      int ready = 0;
+      if (lane == 0) ready = atomicAdd(&c.tready[slot], 0);
+      ready = __shfl_sync(0xffffffffu, ready, 0);
+      __threadfence();
+      if (ready) {
+        const int32_t k = __ldcg(&c.tcls[slot]);
+        cls = (k >= 0 && same_program(c, k, sm.sig[w], len)) ? k : -2;
+      } else {
+        cls = -3;
+      }
     }
-    cls = __shfl_sync(0xffffffffu, cls, 0);
-    off = __shfl_sync(0xffffffffu, off, 0);
-    if (cls >= 0)
-      for (int x = lane; x < len; x += 32) c.pool[off + x] = sm.sig[w][x];
+    if (lane == 0) {
+      c.row_class[I] = cls;
+      if (cls == -2) atomicAdd(&c.counters[2], 1);
+      if (cls == -3) atomicAdd(&c.counters[4], 1);
+    }
     __syncwarp();
   }
 }
 
-// Phase 3: every row checks its signature against its class's pool entry.
-__global__ void __launch_bounds__(kSigWarps * 32) k_class_assign(ClassArgs c) {
+// The rows k_class_build could not check yet: signature again, compared with
+// the (now complete) pool entry of its key.
+__global__ void __launch_bounds__(kSigWarps * 32) k_class_verify(ClassArgs c) {
   __shared__ SigSmem sm;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t mask = (1u << c.tlog2) - 1u;
   for (int64_t I = (int64_t)blockIdx.x * kSigWarps + w; I < c.n; I += (int64_t)gridDim.x * kSigWarps) {
-    if (c.g.P.rp[I + 1] == c.g.P.rp[I]) {
-      if (lane == 0) c.row_class[I] = -1;
-      continue;
-    }
+    if (c.row_class[I] != -3) continue;
     const int len = compute_sig(c.g, (int32_t)I, sm.sig[w], sm.cand[w], sm.keys[w], c.status);
     int32_t cls = -2;
     if (len > 0) {
@@ -336,16 +381,7 @@ __global__ void __launch_bounds__(kSigWarps * 32) k_class_assign(ClassArgs c) {
         if (k == kEmptyKey) break;
         slot = (slot + 1) & mask;
       }
-      if (found >= 0) {
-        // lengths first (the header fixes the length), then every byte
-        const uint8_t* ref = c.pool + c.class_off[found];
-        const int rlen = program_length(ref);
-        bool same = rlen == len;
-        if (same)
-          for (int x = lane; x < len; x += 32) same &= (ref[x] == sm.sig[w][x]);
-        same = __all_sync(0xffffffffu, same);
-        if (same) cls = found;
-      }
+      if (found >= 0 && same_program(c, found, sm.sig[w], len)) cls = found;
     }
     if (lane == 0) {
       c.row_class[I] = cls;
@@ -471,25 +507,25 @@ int build_classes(ptap_plan* p, const ptap_csr* A, const ptap_csr* P, cudaStream
   const int64_t tcap = (int64_t)1 << tlog2;
   const int64_t pool_cap = (int64_t)1 << 20;
   unsigned long long* tkey = nullptr;
-  int32_t *trep = nullptr, *tcls = nullptr, *counters = nullptr, *row_class = nullptr;
+  int32_t *tready = nullptr, *tcls = nullptr, *counters = nullptr, *row_class = nullptr;
   int32_t* class_off = nullptr;
   uint8_t* pool = nullptr;
   PTAP_TRY(sc.get(&tkey, tcap));
-  PTAP_TRY(sc.get(&trep, tcap));
+  PTAP_TRY(sc.get(&tready, tcap));
   PTAP_TRY(sc.get(&tcls, tcap));
-  PTAP_TRY(sc.get(&counters, 4));
+  PTAP_TRY(sc.get(&counters, 8));
   PTAP_TRY(sc.get(&row_class, p->n));
   PTAP_TRY(sc.get(&class_off, tcap + 1));
   PTAP_TRY(sc.get(&pool, pool_cap));
   PTAP_CUDA(cudaMemsetAsync(tkey, 0xff, tcap * sizeof(unsigned long long), s));
-  PTAP_CUDA(cudaMemsetAsync(trep, 0x7f, tcap * sizeof(int32_t), s));
-  PTAP_CUDA(cudaMemsetAsync(counters, 0, 4 * sizeof(int32_t), s));
+  PTAP_CUDA(cudaMemsetAsync(tready, 0, tcap * sizeof(int32_t), s));
+  PTAP_CUDA(cudaMemsetAsync(counters, 0, 8 * sizeof(int32_t), s));
   ClassArgs c;
   c.g = SigGeom{CsrI{A->nrows, A->ncols, A->row_ptr, A->col_idx},
                 CsrI{P->nrows, P->ncols, P->row_ptr, P->col_idx}, CsrI{p->m, p->m, p->c_rp, p->c_ci}};
   c.n = p->n;
   c.tkey = tkey;
-  c.trep = trep;
+  c.tready = tready;
   c.tcls = tcls;
   c.tlog2 = tlog2;
   c.pool = pool;
@@ -500,20 +536,19 @@ int build_classes(ptap_plan* p, const ptap_csr* A, const ptap_csr* P, cudaStream
   c.status = p->status;
   // latency-bound warp-per-row work: fill the SMs (16 CTAs of 4 warps each)
   const int grid = num_sms() * 16;
-  k_class_insert<<<grid, kSigWarps * 32, 0, s>>>(c);
+  k_class_build<<<grid, kSigWarps * 32, 0, s>>>(c);
   PTAP_LAUNCHED();
-  int32_t h[4];
+  int32_t h[5];
   PTAP_CUDA(cudaMemcpyAsync(h, counters, sizeof(h), cudaMemcpyDeviceToHost, s));
   PTAP_CUDA(cudaStreamSynchronize(s));
   if (h[2] > 0 || h[3]) return PTAP_OK;  // some row outside the limits, or table full
-  k_class_publish<<<(unsigned)std::min<int64_t>(tcap / kSigWarps, (int64_t)num_sms() * 8), kSigWarps * 32, 0,
-                    s>>>(c);
-  PTAP_LAUNCHED();
-  k_class_assign<<<grid, kSigWarps * 32, 0, s>>>(c);
-  PTAP_LAUNCHED();
-  PTAP_CUDA(cudaMemcpyAsync(h, counters, sizeof(h), cudaMemcpyDeviceToHost, s));
-  PTAP_CUDA(cudaStreamSynchronize(s));
-  if (h[2] > 0 || h[3]) return PTAP_OK;
+  if (h[4] > 0) {  // rows that met their key before its program was published
+    k_class_verify<<<grid, kSigWarps * 32, 0, s>>>(c);
+    PTAP_LAUNCHED();
+    PTAP_CUDA(cudaMemcpyAsync(h, counters, sizeof(h), cudaMemcpyDeviceToHost, s));
+    PTAP_CUDA(cudaStreamSynchronize(s));
+    if (h[2] > 0 || h[3]) return PTAP_OK;
+  }
   const int32_t K = h[0];
   const int32_t pool_used = h[1];
   // Canonical class numbering.  Ids from the concurrent publication above
