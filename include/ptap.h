@@ -112,7 +112,18 @@ typedef struct {
   int32_t general_kernel; /* general owner-mode kernel (rows outside the class programs):
                              0 = sort-based, one warp per fine row (default);
                              1 = hash tables per group of group_lanes lanes */
-  int32_t reserved[4];
+  int32_t compact_chunks; /* L > 0: owner-mode chunks are grown breadth-first over the graph
+                             of C's pattern, by runs of L consecutive coarse rows (L <= 4096),
+                             into compact regions instead of being cut as ranges of
+                             consecutive rows, so fewer fine rows reach two chunks.  Used by
+                             the class-program kernels only: a plan that ends on the general
+                             kernel, has a run of rows longer than a chunk or more chunks
+                             than the packed row locations can name keeps ranges
+                             (ptap_stats.compact_chunks says which).  Plans with
+                             compact chunks are refused (PTAP_ERR_UNSUPPORTED) by
+                             ptap_batch_numeric_noalloc and by batches that mix them with
+                             general-kernel plans; 0: ranges */
+  int32_t reserved[3];
 } ptap_config;
 
 /* Statistics of a plan (host struct filled by ptap_plan_stats). */
@@ -136,6 +147,7 @@ typedef struct {
   int32_t n_specialized;     /* classes running as compiled straight-line code */
   int32_t specialized_permille; /* share of fine-row visits they cover, in 1/1000 */
   int32_t specialize_us;     /* time spent generating and compiling that code */
+  int32_t compact_chunks;    /* 1 if the chunks are grown regions of C's graph */
 } ptap_stats;
 
 typedef struct ptap_plan ptap_plan;

@@ -30,6 +30,7 @@ Config resolve_config(const ptap_config* c) {
   r.debug_checks = c->debug_checks != 0;
   r.cache_indices = c->cache_indices > 0 ? 1 : 0;
   r.general_kernel = c->general_kernel == 1 ? 1 : 0;
+  r.compact_chunks = std::max(0, std::min(c->compact_chunks, 4096));
   r.force_spill = c->force_spill != 0;
   return r;
 }
@@ -76,6 +77,7 @@ int ptap_plan_stats(const ptap_plan* p, ptap_stats* o) {
   o->n_specialized = p->jit_fn ? p->jit_classes : 0;
   o->specialized_permille = p->jit_fn ? (int32_t)(p->jit_coverage * 1000.0 + 0.5) : 0;
   o->specialize_us = (int32_t)std::min(p->jit_ms * 1000.0, 2.0e9);
+  o->compact_chunks = p->compact ? 1 : 0;
   return PTAP_OK;
 }
 

@@ -100,6 +100,10 @@ static int batch_create_t(ptap_batch* b, ptap_plan* const* plans, const ptap_csr
       f.rs_global = nullptr;
       f.jit_slot = nullptr;
       f.aq = p->aq;
+      f.crows = p->compact ? p->chunk_crows : nullptr;
+      f.row_loc = p->compact ? p->row_loc : nullptr;
+      f.chunk_nnz = p->compact ? p->chunk_nnz : nullptr;
+      f.loc_bits = p->loc_bits;
     }
     NumArgs<V>& a = h[q];
     a.A = CsrV<V>{A[q].nrows, A[q].ncols, A[q].row_ptr, A[q].col_idx, (const V*)A[q].val};
@@ -245,6 +249,7 @@ extern "C" int ptap_batch_create(ptap_plan* const* plans, const ptap_csr* A, con
   }
   for (int32_t q = 0; q < count && !all_fast; ++q) {
     const ptap_plan* p = plans[q];
+    if (p->compact) return PTAP_ERR_UNSUPPORTED;  // the general batch kernel takes row ranges
     if (p->cfg.chunk_entries != p0->cfg.chunk_entries || p->cfg.group_lanes != p0->cfg.group_lanes ||
         p->cfg.ap_slots != p0->cfg.ap_slots || p->cfg.block_threads != p0->cfg.block_threads ||
         p->cfg.force_spill != p0->cfg.force_spill)

@@ -407,25 +407,32 @@ __global__ void k_class_remap(int32_t* __restrict__ row_class, int32_t n, const 
   }
 }
 
-// Widest span (last - first fine row) of any chunk's ascending visit list.
+// Widest span (last - first fine row) of any chunk's ascending visit list,
+// into maxspan[0], and the longest list less one, into maxspan[1].
 __global__ void k_chunk_span(const int32_t* __restrict__ fptr, const int32_t* __restrict__ frows,
                              int32_t nch, int32_t* maxspan) {
   for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < nch;
        c += (int64_t)gridDim.x * blockDim.x) {
     const int32_t f0 = fptr[c], f1 = fptr[c + 1];
-    if (f1 > f0) atomicMax(maxspan, frows[f1 - 1] - frows[f0]);
+    if (f1 > f0) {
+      atomicMax(&maxspan[0], frows[f1 - 1] - frows[f0]);
+      atomicMax(&maxspan[1], f1 - 1 - f0);
+    }
   }
 }
 
 // Composite sort key (block of 2^bb consecutive fine rows, class, row): runs
-// of one class stay inside a block.  Small blocks make the warps working on a
+// of one class stay inside a block.  When the rows' span is too wide for the
+// key (compact chunks reach many planes of a mesh), the row's rank in the
+// ascending list stands for its distance from the first (same order; blocks
+// then count visits instead of rows).  Small blocks make the warps working on a
 // chunk at the same time read neighbouring rows of A and P (L1 reuse); large
 // blocks keep runs long (full warps).  bb is a tuning knob (config).
 // The three visit-list kernels below give each chunk a warp, whose lanes
 // stride over the chunk's visits.
 __global__ void k_visit_keys(const int32_t* __restrict__ fptr, const int32_t* __restrict__ frows,
                              int32_t nch, const int32_t* __restrict__ row_class, int shift,
-                             int kBlockBits, int32_t* keys) {
+                             int kBlockBits, bool rank, int32_t* keys) {
   const int lane = threadIdx.x & 31;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < nch; c += nw) {
@@ -433,7 +440,7 @@ __global__ void k_visit_keys(const int32_t* __restrict__ fptr, const int32_t* __
     if (f0 == f1) continue;
     const int32_t base = frows[f0];  // lists are ascending before this sort
     for (int32_t f = f0 + lane; f < f1; f += 32) {
-      const int32_t I = frows[f], d = I - base;
+      const int32_t I = frows[f], d = rank ? f - f0 : I - base;
       keys[f] = ((d >> kBlockBits) << (shift + kBlockBits)) | (row_class[I] << kBlockBits) |
                 (d & ((1 << kBlockBits) - 1));
     }
@@ -594,12 +601,22 @@ int build_classes(ptap_plan* p, const ptap_csr* A, const ptap_csr* P, cudaStream
   int kb = 1;
   while ((1 << kb) <= K) ++kb;
   const int shift = kb;  // class field width
-  PTAP_CUDA(cudaMemsetAsync(counters, 0, sizeof(int32_t), s));
+  PTAP_CUDA(cudaMemsetAsync(counters, 0, 2 * sizeof(int32_t), s));
   k_chunk_span<<<grid, 256, 0, s>>>(p->chunk_fptr, p->chunk_frows, p->nchunks, counters);
   PTAP_LAUNCHED();
-  int32_t maxspan = 0;
-  PTAP_CUDA(cudaMemcpyAsync(&maxspan, counters, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  int32_t spans[2] = {0, 0};
+  PTAP_CUDA(cudaMemcpyAsync(spans, counters, sizeof(spans), cudaMemcpyDeviceToHost, s));
   PTAP_CUDA(cudaStreamSynchronize(s));
+  int32_t maxspan = spans[0];
+  bool rank = false;
+  {
+    int need = 0;
+    while (((int64_t)1 << need) <= (int64_t)maxspan) ++need;
+    if (need + kb > 31) {
+      maxspan = spans[1];
+      rank = true;
+    }
+  }
   // key bits: block (d >> bb) | class (kb bits) | d & (2^bb - 1), all below bit 31;
   // bb defaults to the whole chunk span (class-major order)
   int kBlockBits = p->cfg.visit_block_log2 > 0 ? p->cfg.visit_block_log2 : 31 - kb;
@@ -617,7 +634,7 @@ int build_classes(ptap_plan* p, const ptap_csr* A, const ptap_csr* P, cudaStream
   PTAP_TRY(sc.get(&flag, p->nfrows));
   PTAP_TRY(sc.get(&segid, p->nfrows + 1));
   k_visit_keys<<<grid, 256, 0, s>>>(p->chunk_fptr, p->chunk_frows, p->nchunks, row_class, shift,
-                                    kBlockBits, keys);
+                                    kBlockBits, rank, keys);
   PTAP_LAUNCHED();
   PTAP_TRY(segmented_sort(p->mem, p->chunk_fptr, p->nchunks, keys, p->chunk_frows, -1, s));
   k_seg_flags<<<grid, 256, 0, s>>>(p->chunk_fptr, p->nchunks, keys, shift, kBlockBits, flag);

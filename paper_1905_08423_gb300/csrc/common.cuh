@@ -148,6 +148,7 @@ struct Config {
   int force_spill = 0;
   int cache_indices = 0;      // store P's row start for every entry of A (fast path)
   int general_kernel = 0;     // general path: 0 sort-based (warp per row), 1 hash groups
+  int compact_chunks = 0;     // > 0: chunks grown over C's graph, by runs of this many rows
 };
 
 Config resolve_config(const ptap_config* c);
@@ -192,7 +193,16 @@ struct ptap_plan {
 
   // owner-mode numeric schedule
   int32_t nchunks = 0, nheavy = 0, max_chunk_rows = 0, max_chunk_nnz = 0;
-  int32_t* chunk_row = nullptr;   // [nchunks+1] first coarse row of each chunk
+  int32_t* chunk_row = nullptr;   // [nchunks+1] first coarse row of each chunk (ranges), or
+                                  // first entry of the chunk in chunk_crows (compact chunks)
+  // compact chunks (symbolic.cu): rows of each chunk, ascending; per coarse
+  // row its chunk and accumulator offset packed as chunk << loc_bits | offset;
+  // C entries per chunk
+  bool compact = false;
+  int32_t loc_bits = 0;
+  int32_t* chunk_crows = nullptr;
+  int32_t* row_loc = nullptr;
+  int32_t* chunk_nnz = nullptr;
   int32_t* chunk_fptr = nullptr;  // [nchunks+1] offsets into chunk_frows
   int32_t* chunk_frows = nullptr; // fine rows visited per chunk, ascending
   int64_t nfrows = 0;

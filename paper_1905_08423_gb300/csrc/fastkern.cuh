@@ -72,6 +72,15 @@ struct FastArgs {
   // Optional cached index: aq[e] = P.rp[A.ci[e]] for every entry e of A
   // (null: looked up through A.ci).
   const int32_t* aq;
+  // Optional compact chunks.  When row_loc is set, the coarse rows of chunk c
+  // are crows[chunk_row[c] .. chunk_row[c+1]) (ascending), row_loc[i] =
+  // chunk << loc_bits | offset of row i's first entry in that chunk's
+  // accumulator, and chunk_nnz[c] is the chunk's entries.  Null: chunk c is
+  // the range of coarse rows [chunk_row[c], chunk_row[c+1]).
+  const int32_t* crows;
+  const int32_t* row_loc;
+  const int32_t* chunk_nnz;
+  int32_t loc_bits;
 };
 
 // Adds v to *p, p in shared memory.  A relaxed reduction: the barrier that
@@ -110,6 +119,8 @@ __device__ __forceinline__ void interp_add(double* p, double w, double r) {
 
 // Interpreter: 32 fine rows [f, min(f+32, f1)) of one class, one per lane.
 // R is the lane's row of A P, lane-major in shared memory (R[t*32 + lane]).
+// The chunk is the coarse rows [i0, i1) with row offsets roff, or, with
+// compact chunks, chunk number i0 (i1 and roff unused).
 template <typename V>
 __device__ __forceinline__ void fast_piece(const FastArgs<V>& a, const uint8_t* prog, V* R, int32_t f,
                                            int32_t f1, int32_t i0, int32_t i1, V* acc,
@@ -165,7 +176,14 @@ __device__ __forceinline__ void fast_piece(const FastArgs<V>& a, const uint8_t* 
     if (s < pI) {
       const int32_t i = a.P.ci[rp + s];
       ws[s] = a.P.val[rp + s];
-      if (valid && i >= i0 && i < i1) cb[s] = roff[i - i0];
+      if (valid) {
+        if (a.row_loc) {
+          const int32_t l = a.row_loc[i];
+          if ((l >> a.loc_bits) == i0) cb[s] = l & ((1 << a.loc_bits) - 1);
+        } else if (i >= i0 && i < i1) {
+          cb[s] = roff[i - i0];
+        }
+      }
     }
   }
   for (int t = 0; t < r; ++t) {
@@ -218,17 +236,29 @@ struct FastSmem {
 // One chunk c of a product.  `special(a, cls, f, f1, i0, i1, acc, roff, I)`
 // runs a piece of a class it has straight-line code for and returns true;
 // otherwise the interpreter runs it from the class's program.  I is the
-// lane's fine row of the piece, loaded one piece ahead.
+// lane's fine row of the piece, loaded one piece ahead.  With compact chunks
+// i0 is the chunk number and the values go back to C row by row.
 template <typename V, typename Special>
 __device__ __forceinline__ void fast_chunk(const FastArgs<V>& a, int32_t c, FastSmem<V>& sm,
                                            Special special) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
   V* acc = sm.acc;
   int32_t* roff = sm.roff;
-  const int32_t i0 = a.chunk_row[c], i1 = a.chunk_row[c + 1];
-  const int32_t base = a.c_rp[i0], nnz = a.c_rp[i1] - base;
+  const bool compact = a.row_loc != nullptr;
+  int32_t i0, i1, base = 0, nnz;
+  if (compact) {
+    i0 = c;
+    i1 = 0;
+    nnz = a.chunk_nnz[c];
+  } else {
+    i0 = a.chunk_row[c];
+    i1 = a.chunk_row[c + 1];
+    base = a.c_rp[i0];
+    nnz = a.c_rp[i1] - base;
+  }
   for (int t = threadIdx.x; t < nnz; t += blockDim.x) acc[t] = V(0);
-  for (int t = threadIdx.x; t <= i1 - i0; t += blockDim.x) roff[t] = a.c_rp[i0 + t] - base;
+  if (!compact)
+    for (int t = threadIdx.x; t <= i1 - i0; t += blockDim.x) roff[t] = a.c_rp[i0 + t] - base;
   __syncthreads();
   // the chunk's pieces (<= 32 rows of one class) go round-robin to the warps
   int32_t loaded = -1;
@@ -271,7 +301,29 @@ __device__ __forceinline__ void fast_chunk(const FastArgs<V>& a, int32_t c, Fast
     I = In;
   }
   __syncthreads();
-  for (int t = threadIdx.x; t < nnz; t += blockDim.x) a.c_val[base + t] = acc[t];
+  if (compact) {
+    // 32 coarse rows per warp step: each lane looks up one row's place in C
+    // and in the accumulator, then the warp copies the rows one by one
+    const int32_t mask = (1 << a.loc_bits) - 1;
+    const int32_t r1 = a.chunk_row[c + 1];
+    for (int32_t j0 = a.chunk_row[c] + warp * 32; j0 < r1; j0 += nwarps * 32) {
+      int32_t b = 0, len = 0, off = 0;
+      if (j0 + lane < r1) {
+        const int32_t i = a.crows[j0 + lane];
+        b = a.c_rp[i];
+        len = a.c_rp[i + 1] - b;
+        off = a.row_loc[i] & mask;
+      }
+      const int nr = min(32, r1 - j0);
+      for (int r = 0; r < nr; ++r) {
+        const int32_t br = __shfl_sync(0xffffffffu, b, r), lr = __shfl_sync(0xffffffffu, len, r),
+                      orr = __shfl_sync(0xffffffffu, off, r);
+        for (int32_t x = lane; x < lr; x += 32) a.c_val[br + x] = acc[orr + x];
+      }
+    }
+  } else {
+    for (int t = threadIdx.x; t < nnz; t += blockDim.x) a.c_val[base + t] = acc[t];
+  }
   __syncthreads();
 }
 

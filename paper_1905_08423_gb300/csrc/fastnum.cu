@@ -54,6 +54,10 @@ static FastArgs<V> fast_args(ptap_plan* p, const ptap_csr* A, const ptap_csr* P,
   a.rs_global = (V*)p->interp_rs;
   a.jit_slot = p->jit_slot;
   a.aq = p->aq;
+  a.crows = p->compact ? p->chunk_crows : nullptr;
+  a.row_loc = p->compact ? p->row_loc : nullptr;
+  a.chunk_nnz = p->compact ? p->chunk_nnz : nullptr;
+  a.loc_bits = p->loc_bits;
   return a;
 }
 

@@ -177,7 +177,7 @@ void appendf(std::string& o, const char* fmt, ...) {
 // at offsets sigma(s, t) read from a per-class constant table (Alg. 8).  The
 // loop keeps the code of a class near r accumulations instead of r * pI: the
 // instruction cache, not the issue rate, limits how many classes pay off.
-std::string gen_class(int cls, const uint8_t* g, bool cached) {
+std::string gen_class(int cls, const uint8_t* g, bool cached, int loc_bits) {
   const int na = g[0], r = g[1], pI = g[2];
   const uint8_t* pa = g + 8;
   const uint8_t* tsec = g + 8 + ((na + 7) & ~7);
@@ -209,14 +209,28 @@ std::string gen_class(int cls, const uint8_t* g, bool cached) {
         if (tsec[x * 8 + b] == t) appendf(o, "  R%d += a%d * Pv[q%d + %d];\n", t, x, x, b);
   }
   // outer product: the next entry of P(I,:) is loaded while this one is added
-  o += "  const int32_t rp = a.P.rp[I];\n  int32_t in = a.P.ci[rp];\n  V wn = a.P.val[rp];\n";
-  appendf(o,
-          "#pragma unroll 1\n  for (int s = 0; s < %d; ++s) {\n"
-          "    const int32_t i = in;\n    const V w = wn;\n"
-          "    if (s + 1 < %d) {\n      in = a.P.ci[rp + s + 1];\n      wn = a.P.val[rp + s + 1];\n    }\n"
-          "    if (valid && i >= i0 && i < i1) {\n      V* c = acc + roff[i - i0];\n"
-          "      const unsigned char* sg = sg_%d + s * %d;\n",
-          pI, pI, cls, r);
+  o += "  const int32_t rp = a.P.rp[I];\n";
+  if (loc_bits > 0) {
+    // compact chunks: i0 is the chunk number; row_loc packs (chunk, offset)
+    o += "  int32_t ln = a.row_loc[a.P.ci[rp]];\n  V wn = a.P.val[rp];\n  (void)i1;\n  (void)roff;\n";
+    appendf(o,
+            "#pragma unroll 1\n  for (int s = 0; s < %d; ++s) {\n"
+            "    const int32_t l = ln;\n    const V w = wn;\n"
+            "    if (s + 1 < %d) {\n      ln = a.row_loc[a.P.ci[rp + s + 1]];\n      wn = a.P.val[rp + s + 1];\n"
+            "    }\n"
+            "    if (valid && (l >> %d) == i0) {\n      V* c = acc + (l & %d);\n"
+            "      const unsigned char* sg = sg_%d + s * %d;\n",
+            pI, pI, loc_bits, (1 << loc_bits) - 1, cls, r);
+  } else {
+    o += "  int32_t in = a.P.ci[rp];\n  V wn = a.P.val[rp];\n";
+    appendf(o,
+            "#pragma unroll 1\n  for (int s = 0; s < %d; ++s) {\n"
+            "    const int32_t i = in;\n    const V w = wn;\n"
+            "    if (s + 1 < %d) {\n      in = a.P.ci[rp + s + 1];\n      wn = a.P.val[rp + s + 1];\n    }\n"
+            "    if (valid && i >= i0 && i < i1) {\n      V* c = acc + roff[i - i0];\n"
+            "      const unsigned char* sg = sg_%d + s * %d;\n",
+            pI, pI, cls, r);
+  }
   for (int t = 0; t < r; ++t) appendf(o, "      acc_fma(c + sg[%d], w, R%d);\n", t, t);
   o += "    }\n  }\n}\n";
   return o;
@@ -276,7 +290,7 @@ int jit_prepare(ptap_plan* p) {
   // source
   std::string src = "#include \"fastkern.cuh\"\nusing namespace ptapk;\n";
   src += p->dtype == PTAP_F64 ? "typedef double V;\n" : "typedef float V;\n";
-  for (size_t i = 0; i < hot.size(); ++i) src += gen_class((int)i, prog(hot[i]), p->aq != nullptr);
+  for (size_t i = 0; i < hot.size(); ++i) src += gen_class((int)i, prog(hot[i]), p->aq != nullptr, p->compact ? p->loc_bits : 0);
   src += "struct Special {\n  __device__ bool operator()(const FastArgs<V>& a, int32_t cls, int32_t f, int32_t f1,"
          " int32_t i0, int32_t i1, V* acc, const int32_t* roff, int32_t I) const {\n"
          "    switch (a.jit_slot[cls]) {\n";

@@ -156,6 +156,7 @@ extern "C" int ptap_batch_numeric_noalloc(ptap_plan* const* plans, const ptap_cs
   for (int32_t q = 0; q < count; ++q) {
     const ptap_plan* p = plans[q];
     if (!p || p->kind != 0 || p->dtype != p0->dtype) return PTAP_ERR_INVALID;
+    if (p->compact) return PTAP_ERR_UNSUPPORTED;  // the general owner kernel takes row ranges
     if (p->cfg.chunk_entries != p0->cfg.chunk_entries || p->cfg.group_lanes != p0->cfg.group_lanes ||
         p->cfg.ap_slots != p0->cfg.ap_slots || p->cfg.block_threads != p0->cfg.block_threads ||
         p->cfg.force_spill != p0->cfg.force_spill)

@@ -590,17 +590,31 @@ __global__ void k_row_chunk(const int32_t* __restrict__ chunk_row, int32_t nchun
     row_chunk[i] = lo;
   }
 }
-// For each fine row, the distinct chunks among its (sorted) P columns.
-template <bool FILL>
+// For each fine row, the distinct chunks among its (sorted) P columns.  With
+// ranges of rows a chunk's columns are consecutive, so comparing with the
+// previous one suffices.  With compact chunks (ANY) a chunk may recur after
+// another, so each column is compared with all earlier ones of the row; rows
+// longer than kMaxAny set *too_long and are skipped (the caller then falls
+// back to ranges: such rows never run class programs).
+constexpr int kMaxAny = 8;
+template <bool FILL, bool ANY>
 __global__ void k_chunk_visits(const int32_t* __restrict__ Prp, const int32_t* __restrict__ Pci,
                                int32_t n, const int32_t* __restrict__ row_chunk, int32_t* cnt,
-                               const int32_t* __restrict__ fptr, int32_t* frows) {
+                               const int32_t* __restrict__ fptr, int32_t* frows, int32_t* too_long) {
   for (int64_t I = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; I < n;
        I += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t e0 = Prp[I], e1 = Prp[I + 1];
+    if (ANY && e1 - e0 > kMaxAny) {
+      atomicExch(too_long, 1);
+      continue;
+    }
     int32_t prev = -1;
-    for (int32_t e = Prp[I]; e < Prp[I + 1]; ++e) {
+    for (int32_t e = e0; e < e1; ++e) {
       const int32_t c = row_chunk[Pci[e]];
-      if (c != prev) {
+      bool fresh = c != prev;
+      if (ANY)
+        for (int32_t d = e0; d < e && fresh; ++d) fresh = row_chunk[Pci[d]] != c;
+      if (fresh) {
         const int32_t slot = atomicAdd(&cnt[c], 1);
         if (FILL) frows[fptr[c] + slot] = (int32_t)I;
         prev = c;
@@ -609,6 +623,49 @@ __global__ void k_chunk_visits(const int32_t* __restrict__ Prp, const int32_t* _
   }
 }
 }  // namespace
+
+// Visit lists of the chunks given row_chunk (chunk of every coarse row):
+// counts, offsets chunk_fptr, fine rows chunk_frows ascending per chunk.
+// *too_long is set (and nothing built) when ANY and a row of P is longer than
+// kMaxAny.
+template <bool ANY>
+static int build_visits(ptap_plan* p, const ptap_csr* P, const int32_t* row_chunk, bool* too_long,
+                        cudaStream_t s) {
+  const int32_t nch = p->nchunks;
+  Scratch sc(&p->mem);
+  int32_t* cnt = nullptr;
+  PTAP_TRY(sc.get(&cnt, (int64_t)nch + 2));
+  int32_t* flag = cnt + nch + 1;
+  const int grid = num_sms() * 8;
+  PTAP_CUDA(cudaMemsetAsync(cnt, 0, ((size_t)nch + 2) * sizeof(int32_t), s));
+  if (p->n > 0) {
+    k_chunk_visits<false, ANY><<<grid, 256, 0, s>>>(P->row_ptr, P->col_idx, p->n, row_chunk, cnt, nullptr,
+                                                    nullptr, flag);
+    PTAP_LAUNCHED();
+  }
+  *too_long = false;
+  if (ANY) {
+    int32_t f = 0;
+    PTAP_CUDA(cudaMemcpyAsync(&f, flag, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    PTAP_CUDA(cudaStreamSynchronize(s));
+    if (f) {
+      *too_long = true;
+      return PTAP_OK;
+    }
+  }
+  int64_t total = 0;
+  PTAP_TRY(p->mem.get_n(&p->chunk_fptr, (int64_t)nch + 1));
+  PTAP_TRY(exclusive_scan(p->mem, cnt, p->chunk_fptr, nch, &total, s));
+  p->nfrows = total;
+  PTAP_TRY(p->mem.get_n(&p->chunk_frows, total));
+  PTAP_CUDA(cudaMemsetAsync(cnt, 0, ((size_t)nch + 1) * sizeof(int32_t), s));
+  if (p->n > 0) {
+    k_chunk_visits<true, ANY><<<grid, 256, 0, s>>>(P->row_ptr, P->col_idx, p->n, row_chunk, cnt,
+                                                   p->chunk_fptr, p->chunk_frows, flag);
+    PTAP_LAUNCHED();
+  }
+  return segmented_sort(p->mem, p->chunk_fptr, nch, p->chunk_frows, nullptr, -1, s);
+}
 
 static int build_schedule(ptap_plan* p, const ptap_csr* P, cudaStream_t s) {
   const int32_t m = p->m;
@@ -640,39 +697,136 @@ static int build_schedule(ptap_plan* p, const ptap_csr* P, cudaStream_t s) {
   p->max_chunk_rows = max_rows;
   p->max_chunk_nnz = max_nnz;
   PTAP_TRY(p->mem.get_n(&p->chunk_row, (int64_t)nch + 1));
-  PTAP_TRY(p->mem.get_n(&p->chunk_fptr, (int64_t)nch + 1));
   PTAP_CUDA(cudaMemcpyAsync(p->chunk_row, cr.data(), cr.size() * sizeof(int32_t),
                             cudaMemcpyHostToDevice, s));
   if (nch == 0) {
+    PTAP_TRY(p->mem.get_n(&p->chunk_fptr, 1));
     PTAP_CUDA(cudaMemsetAsync(p->chunk_fptr, 0, sizeof(int32_t), s));
     PTAP_TRY(p->mem.get_n(&p->chunk_frows, 1));
     p->nfrows = 0;
     return PTAP_OK;
   }
   Scratch sc(&p->mem);
-  int32_t *row_chunk = nullptr, *cnt = nullptr;
+  int32_t* row_chunk = nullptr;
   PTAP_TRY(sc.get(&row_chunk, m));
-  PTAP_TRY(sc.get(&cnt, (int64_t)nch + 1));
-  const int grid = num_sms() * 8;
-  k_row_chunk<<<grid, 256, 0, s>>>(p->chunk_row, nch, m, row_chunk);
+  k_row_chunk<<<num_sms() * 8, 256, 0, s>>>(p->chunk_row, nch, m, row_chunk);
   PTAP_LAUNCHED();
-  PTAP_CUDA(cudaMemsetAsync(cnt, 0, ((size_t)nch + 1) * sizeof(int32_t), s));
-  if (p->n > 0) {
-    k_chunk_visits<false><<<grid, 256, 0, s>>>(P->row_ptr, P->col_idx, p->n, row_chunk, cnt, nullptr,
-                                               nullptr);
-    PTAP_LAUNCHED();
+  bool unused = false;
+  return build_visits<false>(p, P, row_chunk, &unused, s);
+}
+
+// Compact chunks: regions of the graph of C's pattern (row i adjacent to the
+// columns of C(i,:)), grown breadth-first over runs of L consecutive coarse
+// rows (L = compact_chunks) from the lowest run not yet taken, until the next
+// run reached would overflow the chunk.  On a mesh the regions are blocks of
+// coarse points instead of slabs, so fewer fine rows have P(I,:) entries in
+// two chunks (each such visit recomputes the row of A P); runs keep a warp's
+// fine rows, which lie along the fastest-varying index, on one line of the
+// block.  Sets *done when the plan's schedule was built this way; leaves the
+// plan untouched otherwise (a run longer than a chunk, too many chunks for
+// the packed locations, or a P row too long for the visit lists).
+static int build_schedule_compact(ptap_plan* p, const ptap_csr* P, cudaStream_t s, bool* done) {
+  *done = false;
+  const int32_t m = p->m;
+  const int CH = p->cfg.chunk_entries;
+  if (m == 0 || p->nnz_c == 0) return PTAP_OK;
+  std::vector<int32_t> rp(m + 1), ci(p->nnz_c);
+  PTAP_CUDA(cudaMemcpyAsync(rp.data(), p->c_rp, (m + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  PTAP_CUDA(cudaMemcpyAsync(ci.data(), p->c_ci, ci.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  PTAP_CUDA(cudaStreamSynchronize(s));
+  const int32_t L = std::max(1, p->cfg.compact_chunks);
+  const int32_t nruns = (int32_t)(((int64_t)m + L - 1) / L);
+  auto run_nnz = [&](int32_t r) { return rp[std::min<int64_t>((int64_t)(r + 1) * L, m)] - rp[(int64_t)r * L]; };
+  for (int32_t r = 0; r < nruns; ++r)
+    if (run_nnz(r) > CH) return PTAP_OK;
+  int loc_bits = 1;
+  while ((1 << loc_bits) < CH) ++loc_bits;
+  // grow the regions, a run at a time
+  std::vector<int32_t> own_run(nruns, -1), queue(nruns);
+  int32_t nch = 0;
+  for (int32_t seed = 0; seed < nruns; ++seed) {
+    if (own_run[seed] >= 0) continue;
+    int64_t head = 0, tail = 0, used = run_nnz(seed);
+    own_run[seed] = nch;
+    queue[tail++] = seed;
+    bool full = false;
+    while (head < tail && !full) {
+      const int32_t q = queue[head++];
+      const int32_t i1 = (int32_t)std::min<int64_t>((int64_t)(q + 1) * L, m);
+      for (int32_t e = rp[(int64_t)q * L]; e < rp[i1] && !full; ++e) {
+        const int32_t r = ci[e] / L;
+        if (own_run[r] >= 0) continue;
+        const int32_t len = run_nnz(r);
+        if (used + len > CH) {
+          full = true;
+          break;
+        }
+        own_run[r] = nch;
+        used += len;
+        queue[tail++] = r;
+      }
+    }
+    ++nch;
   }
-  int64_t total = 0;
-  PTAP_TRY(exclusive_scan(p->mem, cnt, p->chunk_fptr, nch, &total, s));
-  p->nfrows = total;
-  PTAP_TRY(p->mem.get_n(&p->chunk_frows, total));
-  PTAP_CUDA(cudaMemsetAsync(cnt, 0, ((size_t)nch + 1) * sizeof(int32_t), s));
-  if (p->n > 0) {
-    k_chunk_visits<true><<<grid, 256, 0, s>>>(P->row_ptr, P->col_idx, p->n, row_chunk, cnt,
-                                              p->chunk_fptr, p->chunk_frows);
-    PTAP_LAUNCHED();
+  std::vector<int32_t> own(m);
+  for (int32_t i = 0; i < m; ++i) own[i] = own_run[i / L];
+  if ((int64_t)nch >= ((int64_t)1 << (31 - loc_bits))) return PTAP_OK;
+  // rows of each chunk ascending, their accumulator offsets, the packed locations
+  std::vector<int32_t> start(nch + 1, 0), nnz(nch, 0), crows(m), loc(m);
+  for (int32_t i = 0; i < m; ++i) ++start[own[i] + 1];
+  for (int32_t c = 0; c < nch; ++c) start[c + 1] += start[c];
+  {
+    std::vector<int32_t> fill(start.begin(), start.end() - 1);
+    for (int32_t i = 0; i < m; ++i) {
+      const int32_t c = own[i];
+      crows[fill[c]++] = i;
+      loc[i] = (c << loc_bits) | nnz[c];
+      nnz[c] += rp[i + 1] - rp[i];
+    }
   }
-  return segmented_sort(p->mem, p->chunk_fptr, nch, p->chunk_frows, nullptr, -1, s);
+  int32_t max_nnz = 0;
+  for (int32_t c = 0; c < nch; ++c) max_nnz = std::max(max_nnz, nnz[c]);
+  Scratch sc(&p->mem);
+  int32_t* row_chunk = nullptr;
+  PTAP_TRY(sc.get(&row_chunk, m));
+  PTAP_CUDA(cudaMemcpyAsync(row_chunk, own.data(), m * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+  p->nchunks = nch;
+  p->nheavy = 0;
+  p->max_chunk_rows = 0;  // no row offsets on chip
+  p->max_chunk_nnz = max_nnz;
+  bool too_long = false;
+  PTAP_TRY(build_visits<true>(p, P, row_chunk, &too_long, s));
+  if (too_long) {
+    p->nchunks = 0;
+    return PTAP_OK;
+  }
+  PTAP_TRY(p->mem.get_n(&p->chunk_row, (int64_t)nch + 1));
+  PTAP_TRY(p->mem.get_n(&p->chunk_crows, m));
+  PTAP_TRY(p->mem.get_n(&p->row_loc, m));
+  PTAP_TRY(p->mem.get_n(&p->chunk_nnz, nch));
+  PTAP_CUDA(cudaMemcpyAsync(p->chunk_row, start.data(), start.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+  PTAP_CUDA(cudaMemcpyAsync(p->chunk_crows, crows.data(), m * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+  PTAP_CUDA(cudaMemcpyAsync(p->row_loc, loc.data(), m * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+  PTAP_CUDA(cudaMemcpyAsync(p->chunk_nnz, nnz.data(), nch * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+  PTAP_CUDA(cudaStreamSynchronize(s));  // the host vectors go out of scope
+  p->loc_bits = loc_bits;
+  p->compact = true;
+  *done = true;
+  return PTAP_OK;
+}
+
+// Drops the owner-mode schedule (to rebuild it another way).
+static void drop_schedule(ptap_plan* p) {
+  int32_t** arrays[] = {&p->chunk_row, &p->chunk_fptr, &p->chunk_frows, &p->chunk_crows, &p->row_loc,
+                        &p->chunk_nnz};
+  for (int32_t** a : arrays) {
+    if (*a) p->mem.put(*a);
+    *a = nullptr;
+  }
+  p->compact = false;
+  p->loc_bits = 0;
+  p->nchunks = 0;
+  p->nfrows = 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -767,17 +921,19 @@ static int symbolic_body(ptap_plan* p, const ptap_csr* A, const ptap_csr* P) {
                                  : (try_fast ? ch_fast : ch_general);
   {
     Range range("ptap: chunk schedule");
-    PTAP_TRY(build_schedule(p, P, s));
+    bool compact = false;
+    if (try_fast && p->cfg.compact_chunks) {
+      PTAP_TRY(build_schedule_compact(p, P, s, &compact));
+      if (!compact) drop_schedule(p);  // whatever a declined attempt left
+    }
+    if (!compact) PTAP_TRY(build_schedule(p, P, s));
   }
   if (try_fast) {
     Range range("ptap: structure classes");
     PTAP_TRY(build_classes(p, A, P, s));
     const int general_ch = user_ch ? std::min(user_value, ch_general_max) : ch_general;
-    if (!p->fast && p->cfg.chunk_entries != general_ch) {
-      p->mem.put(p->chunk_row);
-      p->mem.put(p->chunk_fptr);
-      p->mem.put(p->chunk_frows);
-      p->chunk_row = p->chunk_fptr = p->chunk_frows = nullptr;
+    if (!p->fast && (p->cfg.chunk_entries != general_ch || p->compact)) {
+      drop_schedule(p);
       p->cfg.chunk_entries = general_ch;
       PTAP_TRY(build_schedule(p, P, s));
     }

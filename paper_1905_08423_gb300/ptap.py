@@ -56,7 +56,8 @@ class _Config(_c.Structure):
                 ("force_spill", _c.c_int32), ("class_programs", _c.c_int32),
                 ("visit_block_log2", _c.c_int32), ("specialize", _c.c_int32),
                 ("cache_indices", _c.c_int32), ("general_kernel", _c.c_int32),
-                ("reserved", _c.c_int32 * 4)]
+                ("compact_chunks", _c.c_int32),
+                ("reserved", _c.c_int32 * 3)]
 
 
 class _Stats(_c.Structure):
@@ -70,7 +71,8 @@ class _Stats(_c.Structure):
                 ("ap_slots", _c.c_int32), ("kind", _c.c_int32), ("fast_path", _c.c_int32),
                 ("n_classes", _c.c_int32), ("n_segments", _c.c_int32),
                 ("n_pieces", _c.c_int32), ("n_specialized", _c.c_int32),
-                ("specialized_permille", _c.c_int32), ("specialize_us", _c.c_int32)]
+                ("specialized_permille", _c.c_int32), ("specialize_us", _c.c_int32),
+                ("compact_chunks", _c.c_int32)]
 
 
 _LIB = None
@@ -202,7 +204,8 @@ class Csr:
 
 def make_config(mode=MODE_OWNER, chunk_entries=0, block_threads=0, group_lanes=0, ap_slots=0,
                 debug_checks=False, force_spill=False, class_programs=True,
-                visit_block_log2=0, specialize=False, cache_indices=False, general_kernel=0) -> _Config:
+                visit_block_log2=0, specialize=False, cache_indices=False, general_kernel=0,
+                compact_chunks=False) -> _Config:
     cfg = _Config()
     cfg.mode = mode
     cfg.chunk_entries = chunk_entries
@@ -216,6 +219,7 @@ def make_config(mode=MODE_OWNER, chunk_entries=0, block_threads=0, group_lanes=0
     cfg.specialize = 8 if specialize is True else (-1 if not specialize else int(specialize))
     cfg.cache_indices = int(bool(cache_indices))
     cfg.general_kernel = int(general_kernel)
+    cfg.compact_chunks = 1 if compact_chunks is True else int(compact_chunks)
     return cfg
 
 
