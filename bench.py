@@ -854,6 +854,7 @@ def main():
             cands = [dict(), dict(specialize=8, block_threads=512, chunk_entries=16384),
                      dict(specialize=16, block_threads=512, chunk_entries=16384),
                      dict(specialize=32, block_threads=512, chunk_entries=16384),
+                     dict(specialize=32, block_threads=512, chunk_entries=20480),
                      dict(specialize=32, block_threads=1024, chunk_entries=24576)]
             t64 = autotune.tune(d64A, d64P, candidates=cands, reps=3, warmup=2, cache_path=None,
                                 use_cache=False) if tuned else None

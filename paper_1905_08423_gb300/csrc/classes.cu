@@ -392,10 +392,29 @@ __global__ void __launch_bounds__(kSigWarps * 32) k_class_verify(ClassArgs c) {
 }
 
 // Rows per class (histogram of row_class over the fine rows with a class).
-__global__ void k_class_rows(const int32_t* __restrict__ row_class, int32_t n, int32_t* cnt) {
-  for (int64_t I = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; I < n; I += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t k = row_class[I];
-    if (k >= 0) atomicAdd(&cnt[k], 1);
+// Lanes holding the same class add once for all of them; with `local` (K
+// counters in dynamic shared memory) a CTA counts on chip and then adds its
+// totals to cnt.  The loop bound is uniform over the CTA, so every lane
+// reaches each match.
+__global__ void k_class_rows(const int32_t* __restrict__ row_class, int32_t n, int32_t K, bool local,
+                             int32_t* cnt) {
+  extern __shared__ int32_t hist[];
+  if (local) {
+    for (int32_t k = threadIdx.x; k < K; k += blockDim.x) hist[k] = 0;
+    __syncthreads();
+  }
+  int32_t* out = local ? hist : cnt;
+  const int lane = threadIdx.x & 31;
+  for (int64_t b = (int64_t)blockIdx.x * blockDim.x; b < n; b += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t I = b + threadIdx.x;
+    const int32_t k = I < n ? row_class[I] : -1;
+    const unsigned peers = __match_any_sync(0xffffffffu, k);
+    if (k >= 0 && lane == __ffs(peers) - 1) atomicAdd(&out[k], __popc(peers));
+  }
+  if (local) {
+    __syncthreads();
+    for (int32_t k = threadIdx.x; k < K; k += blockDim.x)
+      if (hist[k]) atomicAdd(&cnt[k], hist[k]);
   }
 }
 
@@ -571,7 +590,9 @@ int build_classes(ptap_plan* p, const ptap_csr* A, const ptap_csr* P, cudaStream
     int32_t* cnt = nullptr;
     PTAP_TRY(sc.get(&cnt, std::max(K, 1)));
     PTAP_CUDA(cudaMemsetAsync(cnt, 0, std::max(K, 1) * sizeof(int32_t), s));
-    k_class_rows<<<grid, 256, 0, s>>>(row_class, p->n, cnt);
+    const bool local = K <= 12288;  // counters within the default 48 KB of shared memory
+    k_class_rows<<<local ? num_sms() * 4 : grid, 256, local ? (size_t)K * sizeof(int32_t) : 0, s>>>(
+        row_class, p->n, K, local, cnt);
     PTAP_LAUNCHED();
     PTAP_CUDA(cudaMemcpyAsync(hoff.data(), class_off, K * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     PTAP_CUDA(cudaMemcpyAsync(hrows.data(), cnt, K * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
