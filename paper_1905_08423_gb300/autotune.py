@@ -4,8 +4,9 @@ The numeric product is repeated many times on one symbolic result (Section
 4.1: one symbolic and eleven numeric products per setup), so a few trial
 products to pick the launch parameters pay for themselves.  ``tune`` builds a
 plan per candidate configuration (chunk size of the on-chip accumulator, CTA
-size, lanes per fine row and hash slots of the general kernel, visit order and
-plan-time specialisation of the class-program kernel, owner or atomic scheme),
+size, lanes per fine row and hash slots of the general kernel, visit order,
+plan-time specialisation and chunk shape (row ranges or compact regions of C's
+graph) of the class-program kernel, owner or atomic scheme),
 times repeated numeric products with CUDA events, and returns the fastest.
 Choices are cached in a JSON file keyed by (GPU name, dtype, problem
 signature); the signature is the shapes, the nonzero counts and a hash of the
@@ -30,7 +31,7 @@ CANDIDATES = [
     dict(specialize=8, block_threads=1024, chunk_entries=32768),
     dict(specialize=16, block_threads=1024, chunk_entries=32768),
     dict(specialize=32, block_threads=1024, chunk_entries=32768),
-
+    dict(specialize=32, block_threads=1024, chunk_entries=32768, compact_chunks=32),
     dict(specialize=4, block_threads=1024, chunk_entries=32768),
     dict(block_threads=512, chunk_entries=16384),
     dict(chunk_entries=4096),
