@@ -84,3 +84,31 @@ def test_host_validation(lib):
     lib.ptap_plan_destroy.argtypes = [ctypes.c_void_p]
     lib.ptap_plan_destroy(None)   # no-op on NULL
 
+
+
+def _struct_fields(name):
+    """Field names, in order, of `typedef struct { ... } name;` in include/ptap.h."""
+    txt = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "ptap.h")).read(), flags=re.S)
+    m = re.search(r"typedef struct \{([^{}]*)\}\s*" + name + r"\s*;", txt)
+    assert m, name
+    fields = []
+    for decl in m.group(1).split(";"):
+        decl = decl.strip()
+        if not decl:
+            continue
+        for part in decl.split(","):
+            fields.append(re.sub(r"\[.*\]", "", part).split()[-1].lstrip("*"))
+    return fields
+
+
+def test_binding_structs_mirror_the_header():
+    """The Python binding's ctypes mirrors list the header's fields in the same order and
+    with the same sizes (a mismatch would shift every later field across the ABI)."""
+    from paper_1905_08423_gb300 import ptap
+    for name, mirror in (("ptap_config", ptap._Config), ("ptap_stats", ptap._Stats)):
+        assert [f for f, _ in mirror._fields_] == _struct_fields(name), name
+    assert ctypes.sizeof(ptap._Config) == 16 * 4       # the config keeps its size
+    cfg = ptap.make_config(compact_chunks=True)
+    assert cfg.compact_chunks == 1
+    assert ptap.make_config(compact_chunks=32).compact_chunks == 32
+    assert ptap.make_config().compact_chunks == 0
