@@ -350,3 +350,19 @@ def test_generators_invariants():
     assert (A5.nrows, A5.nnz, P5.ncols, P5.nnz) == (4096, 20224, 1024, 12032)
     d = A3.to_dense()
     np.testing.assert_array_equal(d, d.T)
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_bound_is_abs_triple_product(seed):
+    """The tolerance bound B = |P|^T |A| |P|: equal to a dense brute force of that product,
+    never below |C| entrywise (triangle inequality), and equal to C when A, P >= 0."""
+    rng = np.random.default_rng(700 + seed)
+    A = pb.random_csr(25, 25, 0.25, rng, int_values=False)
+    P = pb.random_csr(25, 7, 0.3, rng, int_values=False)
+    B = oracle.ptap_bound(A, P).to_dense()
+    Ad, Pd = np.abs(A.to_dense()), np.abs(P.to_dense())
+    np.testing.assert_allclose(B, Pd.T @ Ad @ Pd, rtol=1e-13, atol=0)
+    C = oracle.ptap(A, P).to_dense()
+    assert (np.abs(C) <= B * (1 + 1e-13)).all()
+    Ap, Pp = A.with_values(np.abs(A.val)), P.with_values(np.abs(P.val))
+    np.testing.assert_array_equal(oracle.ptap(Ap, Pp).val, oracle.ptap_bound(A, P).val)
