@@ -595,29 +595,46 @@ __global__ void k_row_chunk(const int32_t* __restrict__ chunk_row, int32_t nchun
 // previous one suffices.  With compact chunks (ANY) a chunk may recur after
 // another, so each column is compared with all earlier ones of the row; rows
 // longer than kMaxAny set *too_long and are skipped (the caller then falls
-// back to ranges: such rows never run class programs).
+// back to ranges: such rows never run class programs).  Neighbouring fine
+// rows mostly reach the same chunks, so the lanes of a warp that add to one
+// chunk's count take their slots with a single atomic.  Loop bounds are
+// uniform over the warp, so every lane reaches each match.
 constexpr int kMaxAny = 8;
 template <bool FILL, bool ANY>
 __global__ void k_chunk_visits(const int32_t* __restrict__ Prp, const int32_t* __restrict__ Pci,
                                int32_t n, const int32_t* __restrict__ row_chunk, int32_t* cnt,
                                const int32_t* __restrict__ fptr, int32_t* frows, int32_t* too_long) {
-  for (int64_t I = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; I < n;
-       I += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t e0 = Prp[I], e1 = Prp[I + 1];
-    if (ANY && e1 - e0 > kMaxAny) {
-      atomicExch(too_long, 1);
-      continue;
+  const int lane = threadIdx.x & 31;
+  for (int64_t b = (int64_t)blockIdx.x * blockDim.x; b < n; b += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t I = b + threadIdx.x;
+    int32_t e0 = 0, len = 0;
+    if (I < n) {
+      e0 = Prp[I];
+      len = Prp[I + 1] - e0;
     }
+    if (ANY && len > kMaxAny) {
+      atomicExch(too_long, 1);
+      len = 0;
+    }
+    const int32_t maxlen = __reduce_max_sync(0xffffffffu, len);
     int32_t prev = -1;
-    for (int32_t e = e0; e < e1; ++e) {
-      const int32_t c = row_chunk[Pci[e]];
-      bool fresh = c != prev;
-      if (ANY)
-        for (int32_t d = e0; d < e && fresh; ++d) fresh = row_chunk[Pci[d]] != c;
-      if (fresh) {
-        const int32_t slot = atomicAdd(&cnt[c], 1);
+    for (int32_t x = 0; x < maxlen; ++x) {
+      int32_t c = -1;
+      if (x < len) {
+        c = row_chunk[Pci[e0 + x]];
+        bool fresh = c != prev;
+        if (ANY)
+          for (int32_t d = 0; d < x && fresh; ++d) fresh = row_chunk[Pci[e0 + d]] != c;
+        if (fresh) prev = c;
+        else c = -1;
+      }
+      const unsigned peers = __match_any_sync(0xffffffffu, c);
+      if (c >= 0) {
+        const int leader = __ffs(peers) - 1;
+        int32_t slot = 0;
+        if (lane == leader) slot = atomicAdd(&cnt[c], __popc(peers));
+        slot = __shfl_sync(peers, slot, leader) + __popc(peers & ((1u << lane) - 1u));
         if (FILL) frows[fptr[c] + slot] = (int32_t)I;
-        prev = c;
       }
     }
   }
