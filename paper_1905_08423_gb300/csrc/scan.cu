@@ -200,17 +200,21 @@ __device__ void cta_bitonic(int32_t* k, int32_t* v, int n) {
   }
 }
 
+// A CTA per listed segment: segments of at most `cap` elements are sorted in
+// dynamic shared memory (cap keys, then cap values when vals is set), longer
+// ones in place in global memory.
 __global__ void k_sort_cta_list(const int32_t* __restrict__ ptr, const int32_t* __restrict__ list,
-                                int32_t nlist, int32_t* keys, int32_t* vals) {
-  __shared__ int32_t sk[kSortSmem];
-  __shared__ int32_t sv[kSortSmem];
+                                int32_t nlist, int32_t* keys, int32_t* vals, int32_t cap) {
+  extern __shared__ int32_t sort_smem[];
+  int32_t* sk = sort_smem;
+  int32_t* sv = sort_smem + cap;
   for (int32_t li = blockIdx.x; li < nlist; li += gridDim.x) {
     const int32_t seg = list[li];
     const int32_t b = ptr[seg], len = ptr[seg + 1] - b;
-    if (len <= kSortSmem) {
+    if (len <= cap) {
       for (int t = threadIdx.x; t < len; t += blockDim.x) {
         sk[t] = keys[b + t];
-        sv[t] = vals ? vals[b + t] : 0;
+        if (vals) sv[t] = vals[b + t];
       }
       __syncthreads();
       cta_bitonic(sk, vals ? sv : nullptr, len);
@@ -225,11 +229,17 @@ __global__ void k_sort_cta_list(const int32_t* __restrict__ ptr, const int32_t* 
   }
 }
 
+// Segments longer than 32 into list; count[0] their number, count[1] the
+// longest length.
 __global__ void k_list_long(const int32_t* __restrict__ ptr, int32_t nseg, int32_t* list,
                             int32_t* count) {
   const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= nseg) return;
-  if (ptr[s + 1] - ptr[s] > 32) list[atomicAdd(count, 1)] = (int32_t)s;
+  const int32_t len = ptr[s + 1] - ptr[s];
+  if (len > 32) {
+    list[atomicAdd(&count[0], 1)] = (int32_t)s;
+    atomicMax(&count[1], len);
+  }
 }
 
 }  // namespace
@@ -246,16 +256,33 @@ int segmented_sort(Tracker& mem, const int32_t* ptr, int32_t nseg, int32_t* keys
   Scratch sc(&mem);
   int32_t *list = nullptr, *cnt = nullptr;
   PTAP_TRY(sc.get(&list, nseg));
-  PTAP_TRY(sc.get(&cnt, 1));
-  PTAP_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int32_t), s));
+  PTAP_TRY(sc.get(&cnt, 2));
+  PTAP_CUDA(cudaMemsetAsync(cnt, 0, 2 * sizeof(int32_t), s));
   k_list_long<<<(unsigned)ceil_div(nseg, 256), 256, 0, s>>>(ptr, nseg, list, cnt);
   PTAP_LAUNCHED();
-  int32_t h = 0;
-  PTAP_CUDA(cudaMemcpyAsync(&h, cnt, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  int32_t h[2] = {0, 0};
+  PTAP_CUDA(cudaMemcpyAsync(h, cnt, sizeof(h), cudaMemcpyDeviceToHost, s));
   PTAP_CUDA(cudaStreamSynchronize(s));
-  if (h > 0) {
-    const int grid = (int)std::min<int64_t>(h, (int64_t)num_sms() * 8);
-    k_sort_cta_list<<<grid, 256, 0, s>>>(ptr, list, h, keys, vals);
+  if (h[0] > 0) {
+    // the shared-memory tile grows to the longest segment, up to the
+    // device's opt-in limit; long tiles get 1024-thread CTAs
+    const int eb = vals ? 8 : 4;
+    int32_t cap = kSortSmem;
+    if (h[1] > kSortSmem) {
+      int dev = 0, optin = 0;
+      PTAP_CUDA(cudaGetDevice(&dev));
+      PTAP_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+      cap = std::max<int32_t>(kSortSmem, std::min<int64_t>(h[1], optin / eb));
+    }
+    const size_t bytes = (size_t)cap * eb;
+    static size_t attr = 48 * 1024;  // largest dynamic size set so far (the default allows 48 KB)
+    if (bytes > attr) {
+      PTAP_CUDA(cudaFuncSetAttribute(k_sort_cta_list, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+      attr = bytes;
+    }
+    const bool big = cap > kSortSmem;
+    const int grid = (int)std::min<int64_t>(h[0], (int64_t)num_sms() * (big ? 1 : 8));
+    k_sort_cta_list<<<grid, big ? 1024 : 256, bytes, s>>>(ptr, list, h[0], keys, vals, cap);
     PTAP_LAUNCHED();
   }
   return PTAP_OK;
