@@ -266,9 +266,20 @@ int ptap_version(void);
  * capture.  Every call shares the array and it keeps the last call's
  * contents: each call clears the work counter itself, and calls whose work
  * overlaps on the GPU race on the array, so callers must serialise them.
+ * The products run on the general owner-mode kernel.  Its on-chip
+ * accumulator also holds column indices, so for plans built with large
+ * chunks (the class-program kernels take up to 32768 entries) it is lowered
+ * to what a CTA's shared memory holds; chunks above that accumulate in C
+ * with atomics instead (same result, slower).
+ * The descriptors and the queue are staged from a process-wide host buffer
+ * that the next call reuses, so while `stream` is capturing the call
+ * launches nothing and returns PTAP_ERR_UNSUPPORTED.
  * Errors: PTAP_ERR_OVERFLOW when count > PTAP_NOALLOC_MAX_PROBLEMS or the
  * plans hold more than PTAP_NOALLOC_MAX_ITEMS owner-mode chunks in total;
- * otherwise as ptap_batch_create.  Asynchronous on `stream`. */
+ * PTAP_ERR_INVALID when the plans differ in dtype or configuration;
+ * PTAP_ERR_UNSUPPORTED for plans with compact chunks, during stream capture,
+ * or when even a 64-entry accumulator does not fit shared memory; otherwise
+ * as ptap_batch_create.  Asynchronous on `stream`. */
 #define PTAP_NOALLOC_SCRATCH_BYTES (8u << 20)
 #define PTAP_NOALLOC_MAX_PROBLEMS 1024
 #define PTAP_NOALLOC_MAX_ITEMS 1000000

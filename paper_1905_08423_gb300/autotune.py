@@ -2,12 +2,16 @@
 
 The numeric product is repeated many times on one symbolic result (Section
 4.1: one symbolic and eleven numeric products per setup), so a few trial
-products to pick the launch parameters pay for themselves.  ``tune`` builds a
-plan per candidate configuration (chunk size of the on-chip accumulator, CTA
-size, lanes per fine row and hash slots of the general kernel, visit order,
-plan-time specialisation and chunk shape (row ranges or compact regions of C's
-graph) of the class-program kernel, owner or atomic scheme),
-times repeated numeric products with CUDA events, and returns the fastest.
+products to pick the launch parameters pay for themselves.
+
+``candidates`` derives the configurations to try from the problem itself:
+one default symbolic pass tells whether the fine rows fall into structure
+classes (the class-program kernels) and how many classes carry the visits;
+the device's opt-in shared memory and the value size bound the on-chip
+accumulator (chunk entries) for each CTA size; the general kernels get their
+lanes per fine row, hash slots and chunk sizes, and the atomic scheme (Alg. 8
+taken literally) is always among them.  ``tune`` builds a plan per candidate,
+times repeated numeric products with CUDA events and returns the fastest.
 Choices are cached in a JSON file keyed by (GPU name, dtype, problem
 signature); the signature is the shapes, the nonzero counts and a hash of the
 row-length sequences of A and P.
@@ -23,21 +27,74 @@ import numpy as np
 
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "ptap_autotune.json")
 
-# Candidate configurations (keyword arguments of ptap.make_config).
-CANDIDATES = [
-    dict(),
-    dict(specialize=8),
-    dict(specialize=8, block_threads=512, chunk_entries=16384),
-    dict(specialize=8, block_threads=1024, chunk_entries=32768),
-    dict(specialize=16, block_threads=1024, chunk_entries=32768),
-    dict(specialize=32, block_threads=1024, chunk_entries=32768),
-    dict(specialize=32, block_threads=1024, chunk_entries=32768, compact_chunks=32),
-    dict(specialize=4, block_threads=1024, chunk_entries=32768),
-    dict(block_threads=512, chunk_entries=16384),
-    dict(chunk_entries=4096),
-    dict(class_programs=False),
-    dict(mode=2, group_lanes=8, ap_slots=32),
-]
+# Shared memory a class-program CTA keeps beside its accumulator (row offsets,
+# per-warp program buffers); the library sizes its largest chunk the same way.
+_FAST_RESERVE = 32 * 1024
+_MAX_CHUNK = 32768
+_GENERAL_MAX_CHUNK = 16384
+
+
+def chunk_limit(value_bytes: int, smem_optin: int) -> int:
+    """Largest class-program chunk (entries) whose accumulator fits the opt-in shared memory."""
+    n = (smem_optin - _FAST_RESERVE) // value_bytes
+    return max(1024, min(_MAX_CHUNK, n & ~1023))
+
+
+def candidate_list(fast_path: bool, n_classes: int, value_bytes: int, smem_optin: int) -> list:
+    """Candidate configurations (ptap.make_config keywords) for one problem.
+
+    fast_path / n_classes come from a default symbolic pass.  For class-program
+    plans: CTAs of 512 and 1024 threads, each with the largest chunk the
+    accumulator allows and smaller ones (fewer entries per CTA: more CTAs for
+    the same C, more fine rows visiting two chunks), and plan-time
+    specialisation of the most visited 16 or 32 classes (fewer if the problem
+    has fewer), plus the interpreter alone.  For plans outside the class
+    programs: the sort-based and the hash-group general kernels over lanes per
+    fine row, hash slots and chunk sizes (class-program plans try the default
+    general kernel only).  The atomic scheme closes both lists.
+    """
+    out = []
+    if fast_path:
+        lim = chunk_limit(value_bytes, smem_optin)
+        spec = sorted({min(16, n_classes), min(32, n_classes)} - {0})
+        for bt in (1024, 512):
+            chunks = sorted({lim, max(1024, (lim * 5 // 6) & ~4095), max(1024, lim // 2)},
+                            reverse=True)
+            for ch in chunks:
+                for k in spec:
+                    out.append(dict(specialize=k, block_threads=bt, chunk_entries=ch))
+        out.append(dict())                                    # interpreter, 256 threads
+        out.append(dict(block_threads=1024, chunk_entries=lim))  # interpreter, large CTAs
+    out.append(dict(class_programs=False))                   # sort-based general kernel
+    if not fast_path:
+        out.append(dict(class_programs=False, chunk_entries=_GENERAL_MAX_CHUNK // 2))
+        for ch in (4096, _GENERAL_MAX_CHUNK // 2):
+            for g, slots in ((8, 64), (16, 128)):
+                out.append(dict(class_programs=False, general_kernel=1, chunk_entries=ch,
+                                group_lanes=g, ap_slots=slots))
+    out.append(dict(mode=2, group_lanes=8, ap_slots=64))     # atomic scatter (Alg. 8)
+    # drop duplicates, keep order
+    seen, uniq = set(), []
+    for c in out:
+        k = json.dumps(c, sort_keys=True)
+        if k not in seen:
+            seen.add(k)
+            uniq.append(c)
+    return uniq
+
+
+def candidates(A, P) -> list:
+    """Candidates for device matrices A, P (ptap.Csr), from one default symbolic pass."""
+    import torch
+
+    from . import ptap
+    plan = ptap.symbolic(A, P)
+    st = plan.stats()
+    plan.destroy()
+    props = torch.cuda.get_device_properties(A.row_ptr.device)
+    optin = int(getattr(props, "shared_memory_per_block_optin", 232448))
+    vb = 8 if A.dtype_code == ptap.F64 else 4
+    return candidate_list(bool(st["fast_path"]), int(st["n_classes"]), vb, optin)
 
 
 def signature(A, P) -> str:
@@ -95,11 +152,14 @@ def _time_numeric(ptap, plan, A, P, C, reps: int, warmup: int) -> float:
 
 
 def tune(A, P, candidates=None, reps: int = 5, warmup: int = 2, cache_path: str | None = DEFAULT_CACHE,
-         use_cache: bool = True) -> TuneResult:
+         use_cache: bool = True, slow_factor: float = 3.0) -> TuneResult:
     """Times each candidate configuration on the device matrices A, P (ptap.Csr).
 
-    Returns the fastest configuration (keyword arguments of ptap.make_config).
-    Candidates that fail (for example by exceeding shared memory) are skipped.
+    ``candidates`` defaults to ``candidates(A, P)``.  Returns the fastest
+    configuration (keyword arguments of ptap.make_config).  A candidate whose
+    first product takes more than ``slow_factor`` times the best so far is
+    recorded with that one time and not repeated.  Candidates that fail (for
+    example by exceeding shared memory) are skipped.
     """
     import torch
 
@@ -111,8 +171,10 @@ def tune(A, P, candidates=None, reps: int = 5, warmup: int = 2, cache_path: str 
     if use_cache and key in cache:
         e = cache[key]
         return TuneResult(dict(e["config"]), float(e["ms"]), [], cached=True)
+    if candidates is None:
+        candidates = globals()["candidates"](A, P)
     best, best_ms, trials, sym = None, float("inf"), [], []
-    for cand in (candidates or CANDIDATES):
+    for cand in candidates:
         try:
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
@@ -121,7 +183,8 @@ def tune(A, P, candidates=None, reps: int = 5, warmup: int = 2, cache_path: str 
             torch.cuda.synchronize()
             sym.append((cand, e0.elapsed_time(e1)))
             C = torch.empty(plan.nnz, dtype=plan.torch_dtype, device=A.row_ptr.device)
-            ms = _time_numeric(ptap, plan, A, P, C, reps, warmup)
+            first = _time_numeric(ptap, plan, A, P, C, 1, 1)
+            ms = first if first > slow_factor * best_ms else _time_numeric(ptap, plan, A, P, C, reps, warmup)
             plan.destroy()
             del C
         except ptap.PtapError as e:

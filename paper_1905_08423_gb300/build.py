@@ -20,6 +20,9 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT, "libptap.so")
+# Measurement tool beside the library: the part's FMA peaks (not on the product's path).
+PROBE_SRC = os.path.join(PKG, "probe", "fma_peak.cu")
+PROBE_LIB = os.path.join(OUT, "libptap_probe.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xptxas", "-O3",
@@ -92,6 +95,10 @@ def build(verbose: bool = False, extra: list[str] | None = None) -> str:
         tmp = LIB + f".{os.getpid()}.tmp"
         run([cc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart", "-ldl"])
         os.replace(tmp, LIB)
+    if _stale(PROBE_LIB, [PROBE_SRC]):
+        tmp = PROBE_LIB + f".{os.getpid()}.tmp"
+        run([cc, *ARCH, *FLAGS, "-shared", PROBE_SRC, "-o", tmp, "-lcudart"])
+        os.replace(tmp, PROBE_LIB)
     return LIB
 
 

@@ -87,10 +87,35 @@ int scratch_address(unsigned char** out) {
 
 template <typename V, int G>
 int launch(ptap_plan* const* plans, const ptap_csr* A, const ptap_csr* P, void* const* C,
-           int32_t count, int64_t nitems, int32_t max_rows, unsigned char* dscratch,
+           int32_t count, int64_t nitems, int32_t max_rows, int32_t max_ch, unsigned char* dscratch,
            cudaStream_t s) {
   Config c = plans[0]->cfg;
+  c.chunk_entries = max_ch;
   c.block_threads = std::min(c.block_threads, 256);  // the kernel's bound
+  // The general owner kernel keeps column indices beside each accumulated
+  // value, so plans built for the class-program kernels (chunks of up to
+  // 32768 entries) can ask for more shared memory than a CTA may have.  The
+  // on-chip capacity is then lowered to what fits: chunks with more entries
+  // than that take the kernel's heavy path, which accumulates in C itself
+  // with atomics (same result, slower).  Settled before anything is staged.
+  int dev = 0, optin = 0;
+  PTAP_CUDA(cudaGetDevice(&dev));
+  PTAP_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  {
+    Config c0 = c;
+    c0.chunk_entries = 0;
+    const size_t fixed = owner_smem_for(plans[0]->dtype, c0, max_rows);
+    if (fixed + 64 * (sizeof(V) + sizeof(int32_t)) > (size_t)optin) return PTAP_ERR_UNSUPPORTED;
+    const int64_t fit = ((int64_t)optin - (int64_t)fixed) / (int64_t)(sizeof(V) + sizeof(int32_t));
+    c.chunk_entries = (int)std::max<int64_t>(64, std::min<int64_t>(c.chunk_entries, fit & ~int64_t(63)));
+  }
+  const size_t smem = owner_smem_for(plans[0]->dtype, c, max_rows);
+  PTAP_CUDA(cudaFuncSetAttribute(k_noalloc_batch<V, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem));
+  int per_sm = 0;
+  PTAP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_noalloc_batch<V, G>,
+                                                          c.block_threads, smem));
+  if (per_sm < 1) return PTAP_ERR_UNSUPPORTED;
   NumArgs<V>* desc = (NumArgs<V>*)g_host_stage;
   int32_t* items = (int32_t*)(g_host_stage + (kItemsOffset - kDescOffset));
   int64_t t = 0;
@@ -106,7 +131,7 @@ int launch(ptap_plan* const* plans, const ptap_csr* A, const ptap_csr* P, void* 
     a.chunk_fptr = p->chunk_fptr;
     a.chunk_frows = p->chunk_frows;
     a.nchunks = p->nchunks;
-    a.CH = c.chunk_entries;
+    a.CH = std::min(p->cfg.chunk_entries, c.chunk_entries);
     a.max_rows = max_rows;
     a.status = p->status;
     for (int32_t ch = 0; ch < p->nchunks; ++ch) {
@@ -115,13 +140,6 @@ int launch(ptap_plan* const* plans, const ptap_csr* A, const ptap_csr* P, void* 
       ++t;
     }
   }
-  const size_t smem = owner_smem_for(plans[0]->dtype, c, max_rows);
-  PTAP_CUDA(cudaFuncSetAttribute(k_noalloc_batch<V, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem));
-  int per_sm = 0;
-  PTAP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_noalloc_batch<V, G>,
-                                                          c.block_threads, smem));
-  if (per_sm < 1) return PTAP_ERR_INVALID;
   // the counter must start at zero: the array keeps the previous call's value
   PTAP_CUDA(cudaMemsetAsync(dscratch, 0, kDescOffset, s));
   PTAP_CUDA(cudaMemcpyAsync(dscratch + kDescOffset, desc, (size_t)count * sizeof(NumArgs<V>),
@@ -152,36 +170,44 @@ extern "C" int ptap_batch_numeric_noalloc(ptap_plan* const* plans, const ptap_cs
   const ptap_plan* p0 = plans[0];
   if (!p0) return PTAP_ERR_INVALID;
   int64_t nitems = 0;
-  int32_t max_rows = 1;
+  int32_t max_rows = 1, max_ch = 64;
   for (int32_t q = 0; q < count; ++q) {
     const ptap_plan* p = plans[q];
     if (!p || p->kind != 0 || p->dtype != p0->dtype) return PTAP_ERR_INVALID;
     if (p->compact) return PTAP_ERR_UNSUPPORTED;  // the general owner kernel takes row ranges
-    if (p->cfg.chunk_entries != p0->cfg.chunk_entries || p->cfg.group_lanes != p0->cfg.group_lanes ||
-        p->cfg.ap_slots != p0->cfg.ap_slots || p->cfg.block_threads != p0->cfg.block_threads ||
+    // one kernel instance serves every plan: the lanes per fine row and the hash
+    // slots are compiled into it (chunk sizes and CTA sizes may differ)
+    if (p->cfg.group_lanes != p0->cfg.group_lanes || p->cfg.ap_slots != p0->cfg.ap_slots ||
         p->cfg.force_spill != p0->cfg.force_spill)
       return PTAP_ERR_INVALID;
+    max_ch = std::max(max_ch, p->cfg.chunk_entries);
     PTAP_TRY(check_numeric_inputs(p, &A[q], &P[q]));
     if (p->nnz_c > 0 && !C_vals[q]) return PTAP_ERR_INVALID;
     nitems += p->nchunks;
     max_rows = std::max(max_rows, p->max_chunk_rows);
   }
   if (nitems > PTAP_NOALLOC_MAX_ITEMS) return PTAP_ERR_OVERFLOW;
+  cudaStream_t s = (cudaStream_t)stream;
+  // The descriptors and the queue are copied from a process-wide host buffer
+  // that the next call overwrites; a captured copy would read it at replay,
+  // with another call's contents.  So this call is refused during capture.
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  PTAP_CUDA(cudaStreamIsCapturing(s, &cap));
+  if (cap != cudaStreamCaptureStatusNone) return PTAP_ERR_UNSUPPORTED;
   std::lock_guard<std::mutex> lock(g_mutex);
   unsigned char* dscratch = nullptr;
   PTAP_TRY(scratch_address(&dscratch));
-  cudaStream_t s = (cudaStream_t)stream;
   const int g = p0->cfg.group_lanes;
   if (p0->dtype == PTAP_F64) {
-    if (g == 4) return launch<double, 4>(plans, A, P, C_vals, count, nitems, max_rows, dscratch, s);
-    if (g == 8) return launch<double, 8>(plans, A, P, C_vals, count, nitems, max_rows, dscratch, s);
-    if (g == 16) return launch<double, 16>(plans, A, P, C_vals, count, nitems, max_rows, dscratch, s);
-    if (g == 32) return launch<double, 32>(plans, A, P, C_vals, count, nitems, max_rows, dscratch, s);
+    if (g == 4) return launch<double, 4>(plans, A, P, C_vals, count, nitems, max_rows, max_ch, dscratch, s);
+    if (g == 8) return launch<double, 8>(plans, A, P, C_vals, count, nitems, max_rows, max_ch, dscratch, s);
+    if (g == 16) return launch<double, 16>(plans, A, P, C_vals, count, nitems, max_rows, max_ch, dscratch, s);
+    if (g == 32) return launch<double, 32>(plans, A, P, C_vals, count, nitems, max_rows, max_ch, dscratch, s);
   } else {
-    if (g == 4) return launch<float, 4>(plans, A, P, C_vals, count, nitems, max_rows, dscratch, s);
-    if (g == 8) return launch<float, 8>(plans, A, P, C_vals, count, nitems, max_rows, dscratch, s);
-    if (g == 16) return launch<float, 16>(plans, A, P, C_vals, count, nitems, max_rows, dscratch, s);
-    if (g == 32) return launch<float, 32>(plans, A, P, C_vals, count, nitems, max_rows, dscratch, s);
+    if (g == 4) return launch<float, 4>(plans, A, P, C_vals, count, nitems, max_rows, max_ch, dscratch, s);
+    if (g == 8) return launch<float, 8>(plans, A, P, C_vals, count, nitems, max_rows, max_ch, dscratch, s);
+    if (g == 16) return launch<float, 16>(plans, A, P, C_vals, count, nitems, max_rows, max_ch, dscratch, s);
+    if (g == 32) return launch<float, 32>(plans, A, P, C_vals, count, nitems, max_rows, max_ch, dscratch, s);
   }
   return PTAP_ERR_INVALID;
 }

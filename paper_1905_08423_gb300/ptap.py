@@ -349,11 +349,24 @@ def backward(plan: Plan, A: Csr, P: Csr, G: torch.Tensor, need_dA=True, need_dP=
     return dA, dP
 
 
+def _check_outputs(plans, Cs, where: str):
+    """Each C must be a contiguous CUDA tensor of its plan's dtype with room for nnz(C) values:
+    the library writes through the raw pointers."""
+    if len(plans) != len(Cs):
+        raise PtapError(1, f"{where}: {len(plans)} plans but {len(Cs)} outputs")
+    for q, (p, C) in enumerate(zip(plans, Cs)):
+        if not (isinstance(C, torch.Tensor) and C.is_cuda and C.is_contiguous()
+                and C.dtype == p.torch_dtype and C.numel() >= p.nnz):
+            raise PtapError(1, f"{where}: output {q} must be a contiguous CUDA {p.torch_dtype} "
+                               f"tensor of at least {p.nnz} values")
+
+
 class Batch:
     """ptap_batch_create / ptap_batch_numeric: many products in one persistent launch."""
 
     def __init__(self, plans, As, Ps, Cs, stream=None):
         n = len(plans)
+        _check_outputs(plans, Cs, "ptap_batch_create")
         self._keep = (list(plans), list(As), list(Ps), list(Cs))
         hp = (_VP * n)(*[p.handle for p in plans])
         ca = (_Csr * n)(*[a.c() for a in As])
@@ -416,6 +429,7 @@ def batch_numeric_noalloc(plans, As, Ps, Cs, stream=None):
     f.argtypes = [_c.POINTER(_VP), _c.POINTER(_Csr), _c.POINTER(_Csr), _c.POINTER(_VP),
                   _c.c_int32, _VP]
     n = len(plans)
+    _check_outputs(plans, Cs, "ptap_batch_numeric_noalloc")
     hp = (_VP * n)(*[p.handle for p in plans])
     ca = (_Csr * n)(*[a.c() for a in As])
     cp = (_Csr * n)(*[p.c() for p in Ps])

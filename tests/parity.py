@@ -63,3 +63,45 @@ def run_and_check(A: CSR, P: CSR, dtype=torch.float64, config=None, two_step=Fal
     torch.cuda.synchronize()
     check_values(C2, ref.val, bound.val, dtype)
     return plan, C
+
+
+def sample_rows(m: int, k: int, seed: int) -> np.ndarray:
+    """The first and last 300 coarse rows plus k random ones (sorted, unique)."""
+    rng = np.random.default_rng(seed)
+    head = np.arange(min(300, m))
+    tail = np.arange(max(0, m - 300), m)
+    mid = rng.choice(m, size=min(k, m), replace=False)
+    return np.unique(np.concatenate([head, tail, mid])).astype(np.int32)
+
+
+def sampled_reference(A: CSR, P: CSR, dtype, rows: np.ndarray):
+    """Oracle rows of C and of the bound B = |P|^T|A||P| for the coarse rows ``rows`` (Eq. 8)."""
+    Ar, Pr = rounded(A, dtype), rounded(P, dtype)
+    ref = oracle.ptap_rows(Ar, Pr, rows, PT=oracle.transpose(Pr))
+    Aa, Pa = Ar.abs(), Pr.abs()
+    bnd = oracle.ptap_rows(Aa, Pa, rows, PT=oracle.transpose(Pa))
+    return ref, bnd
+
+
+def check_sampled(plan: ptap.Plan, C: torch.Tensor, ref, bnd, rows: np.ndarray, dtype) -> float:
+    """Row lengths, columns and values of the sampled rows of C against the oracle's."""
+    rp, ci = plan.pattern()
+    rp = rp.cpu().numpy().astype(np.int64)
+    idx = np.concatenate([np.arange(rp[r], rp[r + 1]) for r in rows])
+    it = torch.as_tensor(idx, device=ci.device)
+    got_c = ci[it].cpu().numpy()
+    got_v = C[it].cpu().numpy().astype(np.float64)
+    np.testing.assert_array_equal(np.diff(ref.row_ptr), rp[rows + 1] - rp[rows])
+    np.testing.assert_array_equal(got_c, ref.col_idx)
+    return check_values_np(got_v, ref.val, bnd.val, dtype)
+
+
+def check_values_np(got: np.ndarray, want: np.ndarray, bound: np.ndarray, dtype) -> float:
+    err = np.abs(got - want)
+    ok = np.where(bound > 0, err <= TAU[dtype] * bound, err == 0)
+    if not ok.all():
+        bad = np.nonzero(~ok)[0][:5]
+        raise AssertionError(f"{(~ok).sum()} sampled entries out of tolerance; first {bad}: "
+                             f"got {got[bad]}, want {want[bad]}, bound {bound[bad]}")
+    rel = err / np.where(bound > 0, bound, 1.0)
+    return float(rel.max()) if rel.size else 0.0

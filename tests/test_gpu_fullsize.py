@@ -1,4 +1,6 @@
-"""Full-size parity in the launch configuration the benchmark times.
+"""Full-size parity with the default launch configuration (the configurations
+the autotuner offers, one of which the benchmark times, are covered at full
+size by test_gpu_tuned.py).
 
 At these sizes the oracle computes sampled rows of C one by one (Eq. 8 row
 form); properties that hold at any size are checked on the whole output:
