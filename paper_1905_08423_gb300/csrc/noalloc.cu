@@ -101,6 +101,9 @@ int launch(ptap_plan* const* plans, const ptap_csr* A, const ptap_csr* P, void* 
   int dev = 0, optin = 0;
   PTAP_CUDA(cudaGetDevice(&dev));
   PTAP_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  cudaFuncAttributes fa{};
+  PTAP_CUDA(cudaFuncGetAttributes(&fa, k_noalloc_batch<V, G>));
+  optin -= (int)fa.sharedSizeBytes;  // the kernel's static shared memory counts against the limit
   {
     Config c0 = c;
     c0.chunk_entries = 0;
