@@ -205,21 +205,30 @@ def workload_config(size, n, nnz_a, m, nnz_p, nnz_c, ws):
             "parallelism": f"independent replicas x{ws}" if ws > 1 else "single GPU"}
 
 
-def bench_batch(ptap, pb, dev, tdt, ev, s, count=64, reps=10, probs=None):
-    """64 uneven triple products (sides U{16..96}; 7-/27-point; trilinear/SA P)."""
+def bench_batch(ptap, pb, dev, tdt, ev, s, count=64, reps=10, probs=None, tune=True):
+    """64 uneven triple products (sides U{16..96}; 7-/27-point; trilinear/SA P).
+
+    The launch configuration (one for all plans) is the fastest of the batch
+    tuner's candidates on this mix; the 64 sequential launches use the same plans."""
     import torch
+
+    from paper_1905_08423_gb300 import autotune
     if probs is None:
         probs = pb.batch_problems(seed=4, count=count)
-    As, Ps, plans, Cs = [], [], [], []
-    for A, P in probs:
-        dA, dP = ptap.Csr.from_host(A, dev, tdt), ptap.Csr.from_host(P, dev, tdt)
-        plan = ptap.symbolic(dA, dP)
-        As.append(dA)
-        Ps.append(dP)
-        plans.append(plan)
-        Cs.append(torch.empty(plan.nnz, dtype=tdt, device=dev))
+    As = [ptap.Csr.from_host(A, dev, tdt) for A, _ in probs]
+    Ps = [ptap.Csr.from_host(P, dev, tdt) for _, P in probs]
+    tuned = autotune.tune_batch(list(zip(As, Ps)), reps=3, warmup=2) if tune else None
+    cfg_kw = tuned.config if tuned else {}
+    t0 = time.perf_counter()
+    plans = [ptap.symbolic(a, p, ptap.make_config(**cfg_kw)) for a, p in zip(As, Ps)]
+    Cs = [torch.empty(p.nnz, dtype=tdt, device=dev) for p in plans]
     nnz_c = sum(p.nnz for p in plans)
     batch = ptap.Batch(plans, As, Ps, Cs)
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    vb = 4 if tdt == torch.float32 else 8
+    by = sum(alg_bytes(A.nrows, A.nnz, P.ncols, P.nnz, p.nnz, vb) for (A, P), p in zip(probs, plans))
+    fast = sum(1 for p in plans if p.stats()["fast_path"])
     for _ in range(3):
         batch.numeric()
         for p, a, q, c in zip(plans, As, Ps, Cs):
@@ -262,8 +271,16 @@ def bench_batch(ptap, pb, dev, tdt, ev, s, count=64, reps=10, probs=None):
         p.check()
         p.destroy()
     batch.destroy()
+    hbm_peak, _ = peaks()
     return {"problems": count, "nnz_c_total": nnz_c,
             "rows_total": int(sum(A.nrows for A, _ in probs)),
+            "launch_config": cfg_kw, "class_program_problems": fast,
+            "tuner_ms": ([[c, round(m, 4) if isinstance(m, float) else m] for c, m in tuned.trials]
+                         if tuned else None),
+            "symbolic_and_create_s": round(setup_s, 3),
+            "alg_bytes": by,
+            "roofline": {"bound": "hbm", "achieved": round(by / (bat_ms * 1e-3) / 1e9, 1), "peak": hbm_peak,
+                         "unit": "GB/s", "frac": round(by / (bat_ms * 1e-3) / 1e9 / hbm_peak, 4)},
             "batched": {"ms": round(bat_ms, 4), "c_nnz_per_s": round(nnz_c / (bat_ms * 1e-3), 1)},
             "sequential": {"ms": round(seq_ms, 4), "c_nnz_per_s": round(nnz_c / (seq_ms * 1e-3), 1)},
             "speedup": round(seq_ms / bat_ms, 3),
@@ -271,7 +288,7 @@ def bench_batch(ptap, pb, dev, tdt, ev, s, count=64, reps=10, probs=None):
             "graph_replays": reps, "rescale": "A values x U(0.5, 2) per entry between replays"}
 
 
-def bench_cusparse(A, P, dev, tdt, ev, s, reps=3):
+def bench_cusparse(A, P, dev, tdt, ev, s, reps=3, ours=None):
     """Context only: the two-step product C = P^T (A P) as cuSPARSE SpGEMM calls
     (through torch.sparse), beside this library's own two-step comparator."""
     import warnings
@@ -294,6 +311,7 @@ def bench_cusparse(A, P, dev, tdt, ev, s, reps=3):
         torch.cuda.synchronize()
         peak = torch.cuda.max_memory_allocated() - base
         nnz = int(C._nnz())
+        agree = compare_with_ours(C, ours, tdt) if ours is not None else None
         del C
         a, b = ev(), ev()
         a.record(s)
@@ -304,6 +322,7 @@ def bench_cusparse(A, P, dev, tdt, ev, s, reps=3):
         torch.cuda.synchronize()
         ms = a.elapsed_time(b) / reps
         out = {"ms_per_step": round(ms, 3), "peak_mb": round(peak / 2**20, 1), "nnz_c": nnz,
+               "agrees_with_all_at_once": agree,
                "note": "cuSPARSE SpGEMM via torch.sparse (A P, then P^T (A P)); context, not this library"}
         del tA, tP, tPt
         torch.cuda.empty_cache()
@@ -311,6 +330,26 @@ def bench_cusparse(A, P, dev, tdt, ev, s, reps=3):
     except Exception as e:  # noqa: BLE001 - context only
         torch.cuda.empty_cache()
         return {"unavailable": f"{type(e).__name__}: {str(e)[:200]}"}
+
+
+def compare_with_ours(Ccs, ours, tdt):
+    """cuSPARSE's C against this library's: the same pattern (cuSPARSE keeps every structural
+    entry here, so row pointers and columns must be equal), then values entry by entry
+    within 1e-5 (FP32) or 1e-12 (FP64) of the largest |C| (norm-wise: its summation order
+    differs and entries that cancel are at rounding level)."""
+    import torch
+    rp, ci, val = ours
+    crow = Ccs.crow_indices().to(torch.int32)
+    col = Ccs.col_indices().to(torch.int32)
+    same_pattern = bool(crow.numel() == rp.numel() and col.numel() == ci.numel()
+                        and torch.equal(crow, rp) and torch.equal(col, ci))
+    if not same_pattern:
+        return {"pattern_equal": False}
+    err = (Ccs.values() - val).abs().max().item()
+    scale = val.abs().max().item()
+    tol = 1e-5 if tdt == torch.float32 else 1e-12
+    return {"pattern_equal": True, "max_abs_diff_over_max_abs": err / scale if scale else err,
+            "tol": tol, "agrees": bool(err <= tol * scale)}
 
 
 def alg_fma_general(A, P, dev):
@@ -572,6 +611,32 @@ def oracle_check(A, P, sample):
     return {"agrees": ok, "rows": int(rows.size), "entries": int(sample["ci"].size),
             "pattern_equal": same_pattern, "max_err_over_bound": rel, "tau": tau,
             "oracle_s": round(sec, 2)}
+
+
+def cpu_baselines_other(gpu_ms):
+    """The oracle (FP64 two-step, one host core) on the other configurations, beside the
+    GPU all-at-once time measured for each: the 15^3 model problem, the 200^3 algebraic
+    case and the 512^2 2D case.  ``gpu_ms`` maps a configuration name to its GPU time."""
+    import oracle
+    from paper_1905_08423_gb300 import problems as pb
+    oracle.build()
+    cases = {"model_15": lambda: pb.model_problem(15),
+             "algebraic_200": lambda: pb.algebraic_problem(200, seed=3),
+             "poisson2d_512": lambda: pb.poisson2d_problem(512)}
+    out = {}
+    for name, make in cases.items():
+        A, P = make()
+        reps = 5 if A.nrows < 1_000_000 else 1
+        t = time.perf_counter()
+        for _ in range(reps):
+            C = oracle.ptap(A, P)
+        sec = (time.perf_counter() - t) / reps
+        by = alg_bytes(A.nrows, A.nnz, P.ncols, P.nnz, C.nnz, 8)
+        g = gpu_ms.get(name)
+        out[name] = {"oracle_s": round(sec, 4), "oracle_gbs": round(by / sec / 1e9, 4), "cores": 1,
+                     "nnz_c": int(C.nnz), "gpu_ms": g,
+                     "gpu_over_oracle": (round(sec * 1e3 / g, 1) if g else None)}
+    return out
 
 
 def cpu_baseline(A, P, size, nnz_c, target_s=12.0):
@@ -886,7 +951,10 @@ def main():
         torch.cuda.empty_cache()
 
         # ---- context: the vendor library's two-step SpGEMM on the same input
-        out["cusparse_two_step"] = bench_cusparse(A, P, dev, tdt, ev, s)
+        rp_c, ci_c = plan.pattern()
+        ptap.numeric(plan, dA, dP, C)
+        out["cusparse_two_step"] = bench_cusparse(A, P, dev, tdt, ev, s, ours=(rp_c, ci_c, C))
+        del rp_c, ci_c
 
         # ---- end to end through the C ABI with host buffers (ptap_numeric_host): every
         #      step uploads A's and P's values from pinned memory and downloads C's; the
@@ -1000,10 +1068,30 @@ def main():
                 ptap, pb, dev, other, ev, s, probs=probs)
             del probs
 
+        # ---- FP64 GPU times of the smaller configurations, for the CPU baselines beside them
+        gpu_other_ms = {"algebraic_200": out["algebraic"].get("ms_per_step")}
+        for name, (Ax, Px) in (("model_15", pb.model_problem(15)), ("poisson2d_512", pb.poisson2d_problem(512))):
+            dAx = ptap.Csr.from_host(Ax, dev, torch.float64)
+            dPx = ptap.Csr.from_host(Px, dev, torch.float64)
+            px = ptap.symbolic(dAx, dPx)
+            Cx = torch.empty(px.nnz, dtype=torch.float64, device=dev)
+            for _ in range(3):
+                ptap.numeric(px, dAx, dPx, Cx)
+            a, b = ev(), ev()
+            a.record(s)
+            for _ in range(20):
+                ptap.numeric(px, dAx, dPx, Cx)
+            b.record(s)
+            torch.cuda.synchronize()
+            px.check()
+            gpu_other_ms[name] = round(a.elapsed_time(b) / 20, 4)
+            px.destroy()
+
         # ---- CPU baseline: the oracle on the host cores (rank 0 only)
         if rank == 0:
             out["cpu_baseline"] = cpu_baseline(A, P, args.size, nnz_c)
             out["oracle_check"] = oracle_check(A, P, sample)
+            out["cpu_baseline_other_configs"] = cpu_baselines_other(gpu_other_ms)
             try:
                 out["cpu_baseline_all_cores"] = cpu_baseline_parallel(A, P, nnz_c)
             except Exception as e:  # noqa: BLE001 - a context figure; the single-core one stands

@@ -87,9 +87,10 @@ typedef struct {
 /* Tuning knobs; zero selects the built-in default for a field. */
 typedef struct {
   int32_t mode;           /* PTAP_MODE_* */
-  int32_t chunk_entries;  /* C entries accumulated per CTA in owner mode: 64..32768 (class-program
-                             kernels; clamped so the accumulator fits shared memory, 24576 for
-                             FP64) or 64..16384 (general kernels); 0 = default */
+  int32_t chunk_entries;  /* C entries accumulated per CTA in owner mode: 64..65536 (class-program
+                             kernels; clamped so the accumulator fits shared memory: 49152 for
+                             FP32 and 24576 for FP64 with 227 KB per CTA) or 64..16384
+                             (general kernels); 0 = default */
   int32_t block_threads;  /* threads per CTA of the numeric kernels: 64, 128, 256, or 512/1024
                              for the class-program kernels (the general and batch kernels use
                              at most 256); 0 = default 256 */
@@ -123,7 +124,11 @@ typedef struct {
                              compact chunks are refused (PTAP_ERR_UNSUPPORTED) by
                              ptap_batch_numeric_noalloc and by batches that mix them with
                              general-kernel plans; 0: ranges */
-  int32_t reserved[3];
+  int32_t specialize_scope; /* with specialize = k > 0: 0 = the plan compiles its own kernel
+                               at symbolic time (default); 1 = the plan compiles nothing, and a
+                               batch that includes it (ptap_batch_create) compiles one kernel for
+                               the most visited classes over all its plans */
+  int32_t reserved[2];
 } ptap_config;
 
 /* Statistics of a plan (host struct filled by ptap_plan_stats). */
@@ -268,7 +273,7 @@ int ptap_version(void);
  * overlaps on the GPU race on the array, so callers must serialise them.
  * The products run on the general owner-mode kernel.  Its on-chip
  * accumulator also holds column indices, so for plans built with large
- * chunks (the class-program kernels take up to 32768 entries) it is lowered
+ * chunks (the class-program kernels take up to 49152 entries) it is lowered
  * to what a CTA's shared memory holds; chunks above that accumulate in C
  * with atomics instead (same result, slower).
  * The descriptors and the queue are staged from a process-wide host buffer

@@ -30,7 +30,7 @@ DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "ptap_autotune.j
 # Shared memory a class-program CTA keeps beside its accumulator (row offsets,
 # per-warp program buffers); the library sizes its largest chunk the same way.
 _FAST_RESERVE = 32 * 1024
-_MAX_CHUNK = 32768
+_MAX_CHUNK = 65536
 _GENERAL_MAX_CHUNK = 16384
 
 
@@ -46,7 +46,8 @@ def candidate_list(fast_path: bool, n_classes: int, value_bytes: int, smem_optin
     fast_path / n_classes come from a default symbolic pass.  For class-program
     plans: CTAs of 512 and 1024 threads, each with the largest chunk the
     accumulator allows and smaller ones (fewer entries per CTA: more CTAs for
-    the same C, more fine rows visiting two chunks), and plan-time
+    the same C, more fine rows visiting two chunks), with and without the
+    cached P row start per entry of A at the largest chunk, and plan-time
     specialisation of the most visited 16 or 32 classes (fewer if the problem
     has fewer), plus the interpreter alone.  For plans outside the class
     programs: the sort-based and the hash-group general kernels over lanes per
@@ -57,12 +58,13 @@ def candidate_list(fast_path: bool, n_classes: int, value_bytes: int, smem_optin
     if fast_path:
         lim = chunk_limit(value_bytes, smem_optin)
         spec = sorted({min(16, n_classes), min(32, n_classes)} - {0})
+        mid = 32768 if lim > 32768 else max(1024, (lim * 5 // 6) & ~4095)
         for bt in (1024, 512):
-            chunks = sorted({lim, max(1024, (lim * 5 // 6) & ~4095), max(1024, lim // 2)},
-                            reverse=True)
-            for ch in chunks:
+            for ch in sorted({lim, mid, max(1024, lim // 2)}, reverse=True):
                 for k in spec:
                     out.append(dict(specialize=k, block_threads=bt, chunk_entries=ch))
+            # the plan's cached index (Section 4.2's memory-for-time trade) at the largest chunk
+            out.append(dict(specialize=spec[-1], block_threads=bt, chunk_entries=lim, cache_indices=True))
         out.append(dict())                                    # interpreter, 256 threads
         out.append(dict(block_threads=1024, chunk_entries=lim))  # interpreter, large CTAs
     out.append(dict(class_programs=False))                   # sort-based general kernel
@@ -200,3 +202,69 @@ def tune(A, P, candidates=None, reps: int = 5, warmup: int = 2, cache_path: str 
         cache[key] = {"config": best, "ms": best_ms}
         save_cache(cache, cache_path)
     return TuneResult(best, best_ms, trials, symbolic_ms=sym)
+
+
+def batch_candidate_list(value_bytes: int, smem_optin: int) -> list:
+    """Candidates for a batch of products (ptap.make_config keywords, one config for all plans).
+
+    The interpreter at 256 threads; batch-wide specialisation of the 32 or 64
+    most visited class programs over the whole batch (compiled once, when the
+    batch is created) at 256, 512 and 1024 threads with the chunks each allows;
+    and the general kernel.
+    """
+    lim = chunk_limit(value_bytes, smem_optin)
+    out = [dict()]
+    for k in (32, 64):
+        out.append(dict(specialize=k, specialize_in_batch=True))
+        out.append(dict(specialize=k, specialize_in_batch=True, block_threads=512,
+                        chunk_entries=max(1024, lim // 2)))
+        out.append(dict(specialize=k, specialize_in_batch=True, block_threads=1024, chunk_entries=lim))
+    out.append(dict(class_programs=False))
+    return out
+
+
+def tune_batch(problems, candidates=None, reps: int = 5, warmup: int = 2):
+    """Times one persistent batched launch per candidate over ``problems`` (a list of
+    device (A, P) pairs of one dtype) and returns the fastest configuration."""
+    import torch
+
+    from . import ptap
+    A0 = problems[0][0]
+    if candidates is None:
+        props = torch.cuda.get_device_properties(A0.row_ptr.device)
+        optin = int(getattr(props, "shared_memory_per_block_optin", 232448))
+        candidates = batch_candidate_list(8 if A0.dtype_code == ptap.F64 else 4, optin)
+    best, best_ms, trials = None, float("inf"), []
+    for cand in candidates:
+        plans, batch = [], None
+        try:
+            cfg = ptap.make_config(**cand)
+            plans = [ptap.symbolic(A, P, cfg) for A, P in problems]
+            Cs = [torch.empty(p.nnz, dtype=p.torch_dtype, device=A0.row_ptr.device) for p in plans]
+            batch = ptap.Batch(plans, [a for a, _ in problems], [p for _, p in problems], Cs)
+            for _ in range(warmup):
+                batch.numeric()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record()
+            for _ in range(reps):
+                batch.numeric()
+            e1.record()
+            torch.cuda.synchronize()
+            for p in plans:
+                p.check()
+            ms = e0.elapsed_time(e1) / reps
+        except ptap.PtapError as e:
+            trials.append((cand, str(e)))
+            continue
+        finally:
+            if batch is not None:
+                batch.destroy()
+            for p in plans:
+                p.destroy()
+        trials.append((cand, ms))
+        if ms < best_ms:
+            best, best_ms = dict(cand), ms
+    if best is None:
+        raise RuntimeError("no candidate configuration ran")
+    return TuneResult(best, best_ms, trials)

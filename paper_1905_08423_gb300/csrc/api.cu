@@ -17,11 +17,12 @@ Config resolve_config(const ptap_config* c) {
   Config r;
   if (!c) return r;
   if (c->mode == PTAP_MODE_OWNER || c->mode == PTAP_MODE_ATOMIC) r.mode = c->mode;
-  r.chunk_entries = c->chunk_entries > 0 ? std::min(std::max(c->chunk_entries, 64), 32768) : 0;
+  r.chunk_entries = c->chunk_entries > 0 ? std::min(std::max(c->chunk_entries, 64), 65536) : 0;
   r.class_programs = c->class_programs >= 0 ? 1 : 0;
   r.visit_block_log2 = (c->visit_block_log2 > 0 && c->visit_block_log2 <= 24) ? c->visit_block_log2 : 0;
   r.jit = c->specialize > 0 ? 1 : 0;
   if (c->specialize > 0) r.jit_max_classes = std::min(c->specialize, 256);
+  r.jit_scope = c->specialize_scope == 1 ? 1 : 0;
   const int bt = pick(c->block_threads, r.block_threads);
   r.block_threads = (bt == 64 || bt == 128 || bt == 256 || bt == 512 || bt == 1024) ? bt : r.block_threads;
   const int g = pick(c->group_lanes, r.group_lanes);

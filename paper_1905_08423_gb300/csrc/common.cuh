@@ -141,6 +141,7 @@ struct Config {
   int visit_block_log2 = 0;   // fast path visit order: blocks of 2^b fine rows (0 = class-major)
   int jit = 0;                // specialise the most frequent classes with NVRTC
   int jit_max_classes = 8;
+  int jit_scope = 0;          // 0: the plan's own kernel; 1: only batches compile code
   int block_threads = 256;
   int group_lanes = 8;
   int ap_slots = 64;
@@ -245,17 +246,30 @@ struct ptap_batch {
   ptap::Tracker mem;
   int dtype = PTAP_F64;
   int32_t count = 0;
-  int64_t total_items = 0;
-  void* d_desc = nullptr;     // device array of per-problem descriptors
-  int32_t* d_items = nullptr; // work items: (problem, chunk) pairs, heavy first
-  int32_t* d_counter = nullptr;
   int32_t* status = nullptr;
-  int32_t max_chunk_nnz = 0, max_chunk_rows = 0;
-  ptap::Config cfg;
-  size_t smem = 0;  // launch configuration, settled at creation
-  int grid = 0;
-  bool fast = false;  // every plan runs class programs: the fast batch kernel
-  int fast_ch = 0, fast_maxr = 0, fast_prog_cap = 0;
+  int32_t* d_counter = nullptr;  // two counters: class-program items, general items
+  // Problems whose plans run class programs go through the class-program
+  // batch kernel (interpreted, or specialised for the batch with NVRTC); the
+  // others through the general owner-mode batch kernel.  Each kind has its
+  // own queue of (problem, chunk) items, longest first.
+  int64_t n_fast = 0, n_gen = 0;
+  void* d_desc_fast = nullptr;  // FastArgs per problem (class-program problems)
+  void* d_desc_gen = nullptr;   // NumArgs per problem (general problems)
+  int32_t* d_items_fast = nullptr;
+  int32_t* d_items_gen = nullptr;
+  // class-program kernel
+  int fast_threads = 256, fast_ch = 0, fast_maxr = 1, fast_prog_cap = 16, fast_max_rows = 1;
+  size_t fast_smem = 0;
+  int fast_grid = 0;
+  void* fast_rs = nullptr;   // global scratch for interpreted rows of A P (specialised kernel)
+  void* jit_fn = nullptr;    // ptap_jit_batch, or null: the interpreter kernel runs
+  int jit_classes = 0;
+  double jit_coverage = 0.0;
+  // general kernel
+  ptap::Config cfg;          // lanes per fine row, hash slots, chunk size (largest), 256 threads
+  int32_t max_chunk_rows = 1;
+  size_t gen_smem = 0;
+  int gen_grid = 0;
 };
 
 namespace ptap {

@@ -358,4 +358,29 @@ __device__ __forceinline__ void fast_kernel_body(const FastArgs<V>& a, Special s
   }
 }
 
+// The batched kernel body: chunks of many products from one queue of
+// (problem, chunk) items, longest first, popped with the counter *counter
+// (zero before the launch).  Each problem has its own descriptor; the CTA
+// carve-up is sized for the largest chunk, row of A P, chunk row count and
+// program over the problems, and the interpreter's rows of A P go to `rs`
+// (global scratch) when it is not null.  No CTA waits on another.
+template <typename V, typename Special>
+__device__ __forceinline__ void fast_batch_body(const FastArgs<V>* __restrict__ probs,
+                                                const int32_t* __restrict__ items, int32_t nitems,
+                                                int32_t* counter, int CH, int maxr, int max_rows,
+                                                int prog_cap, V* rs, Special special) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ int32_t item;
+  FastSmem<V> sm(smraw, CH, maxr, max_rows, prog_cap, rs);
+  for (;;) {
+    if (threadIdx.x == 0) item = atomicAdd(counter, 1);
+    __syncthreads();
+    const int32_t it = item;
+    __syncthreads();
+    if (it >= nitems) break;
+    const FastArgs<V> a = probs[items[2 * it]];
+    fast_chunk<V>(a, items[2 * it + 1], sm, special);
+  }
+}
+
 }  // namespace ptapk

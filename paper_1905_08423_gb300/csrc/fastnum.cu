@@ -155,7 +155,9 @@ int jit_launch(ptap_plan* p, const void* args, int grid, cudaStream_t s);
 int prepare_fast(ptap_plan* p) {
   PTAP_TRY(p->dtype == PTAP_F64 ? prepare_fast_t<double>(p) : prepare_fast_t<float>(p));
   PTAP_TRY(prepare_schedule(p));
-  if (p->cfg.jit) jit_prepare(p);  // optional: the interpreter runs if it fails
+  // optional: the interpreter runs if it fails; batch-only specialisation
+  // leaves the compile to ptap_batch_create
+  if (p->cfg.jit && p->cfg.jit_scope == 0) jit_prepare(p);
   return PTAP_OK;
 }
 

@@ -236,61 +236,50 @@ std::string gen_class(int cls, const uint8_t* g, bool cached, int loc_bits) {
   return o;
 }
 
-}  // namespace
 
-// Picks the classes with the most visited rows, generates and compiles the
-// specialised kernel.  Returns PTAP_OK with p->jit_fn set, or any error (the
-// caller then keeps the interpreter).
-int jit_prepare(ptap_plan* p) {
-  std::lock_guard<std::mutex> lock(g_mu);
-  load_apis();
-  if (!g_rtc.ok || !g_drv.ok || !p->fast || p->nclasses <= 0) return PTAP_ERR_UNSUPPORTED;
-  cudaStream_t s = p->stream;
-  // visits per class, from the pieces
-  std::vector<int32_t> meta(p->npieces), off(p->nclasses);
-  PTAP_CUDA(cudaMemcpyAsync(meta.data(), p->piece_meta, meta.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-  PTAP_CUDA(cudaMemcpyAsync(off.data(), p->class_off, off.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-  std::vector<int64_t> visits(p->nclasses, 0);
+// Visits per class of one plan (from its pieces) and its class programs.
+struct ClassTable {
+  std::vector<int64_t> visits;
+  std::vector<int32_t> off;
+  std::vector<uint8_t> pool;
   int64_t total = 0;
-  int pool_len = 0;
-  PTAP_CUDA(cudaStreamSynchronize(s));
-  for (int32_t m : meta) {
-    visits[m >> 6] += m & 63;
-    total += m & 63;
-  }
-  for (int32_t o : off) pool_len = std::max(pool_len, o + p->class_maxlen);
-  std::vector<uint8_t> pool(pool_len);
-  PTAP_CUDA(cudaMemcpy(pool.data(), p->class_pool, pool_len, cudaMemcpyDeviceToHost));
-  // Class ids come from a concurrent deduplication and differ between runs;
-  // the generated source must not, or the disk cache would never hit.  So
-  // classes are ranked by visits with ties broken by program bytes, and the
-  // compiled ones are numbered in program-byte order; a device table maps a
-  // plan's class ids to those numbers.
-  auto prog = [&](int k) { return pool.data() + off[k]; };
-  auto prog_len = [&](int k) {
+  const uint8_t* prog(int k) const { return pool.data() + off[k]; }
+  int len(int k) const {
     const uint8_t* g = prog(k);
     return 8 + ((g[0] + 7) & ~7) + 8 * g[0] + 8 * g[1];
-  };
-  auto prog_less = [&](int x, int y) {
-    return std::lexicographical_compare(prog(x), prog(x) + prog_len(x), prog(y), prog(y) + prog_len(y));
-  };
-  std::vector<int> order(p->nclasses);
-  for (int k = 0; k < p->nclasses; ++k) order[k] = k;
-  std::sort(order.begin(), order.end(),
-            [&](int x, int y) { return visits[x] != visits[y] ? visits[x] > visits[y] : prog_less(x, y); });
-  std::vector<int> hot;
-  int64_t covered = 0;
-  for (int k : order) {
-    if ((int)hot.size() >= p->cfg.jit_max_classes || covered >= total * 99 / 100 || visits[k] == 0) break;
-    hot.push_back(k);
-    covered += visits[k];
   }
-  if (hot.empty()) return PTAP_ERR_UNSUPPORTED;
-  std::sort(hot.begin(), hot.end(), prog_less);
-  // source
+  std::string bytes(int k) const { return std::string((const char*)prog(k), (size_t)len(k)); }
+};
+
+int read_classes(ptap_plan* p, ClassTable& t) {
+  cudaStream_t s = p->stream;
+  std::vector<int32_t> meta(p->npieces);
+  t.off.assign(p->nclasses, 0);
+  PTAP_CUDA(cudaMemcpyAsync(meta.data(), p->piece_meta, meta.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  PTAP_CUDA(cudaMemcpyAsync(t.off.data(), p->class_off, t.off.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  PTAP_CUDA(cudaStreamSynchronize(s));
+  t.visits.assign(p->nclasses, 0);
+  t.total = 0;
+  int pool_len = 0;
+  for (int32_t m : meta) {
+    t.visits[m >> 6] += m & 63;
+    t.total += m & 63;
+  }
+  for (int32_t o : t.off) pool_len = std::max(pool_len, o + p->class_maxlen);
+  t.pool.assign(pool_len, 0);
+  PTAP_CUDA(cudaMemcpy(t.pool.data(), p->class_pool, pool_len, cudaMemcpyDeviceToHost));
+  return PTAP_OK;
+}
+
+// Source of a specialised kernel for the programs `hot` (in this order: the
+// compiled-code numbers are positions in it).  kind 0: one product
+// (ptap_jit_numeric); kind 1: a batch of products (ptap_jit_batch).
+std::string build_source(int dtype, const std::vector<std::string>& hot, bool cached, int loc_bits,
+                         int block_threads, int kind) {
   std::string src = "#include \"fastkern.cuh\"\nusing namespace ptapk;\n";
-  src += p->dtype == PTAP_F64 ? "typedef double V;\n" : "typedef float V;\n";
-  for (size_t i = 0; i < hot.size(); ++i) src += gen_class((int)i, prog(hot[i]), p->aq != nullptr, p->compact ? p->loc_bits : 0);
+  src += dtype == PTAP_F64 ? "typedef double V;\n" : "typedef float V;\n";
+  for (size_t i = 0; i < hot.size(); ++i)
+    src += gen_class((int)i, (const uint8_t*)hot[i].data(), cached, loc_bits);
   src += "struct Special {\n  __device__ bool operator()(const FastArgs<V>& a, int32_t cls, int32_t f, int32_t f1,"
          " int32_t i0, int32_t i1, V* acc, const int32_t* roff, int32_t I) const {\n"
          "    switch (a.jit_slot[cls]) {\n";
@@ -300,10 +289,26 @@ int jit_prepare(ptap_plan* p) {
   // FP32: 64 registers a thread, 1024 resident threads per SM.  FP64 code
   // holds twice the bytes in registers and spills at 64; 128 registers with
   // 512 resident threads measured faster.
-  const int resident = p->dtype == PTAP_F64 ? 512 : 1024;
-  appendf(src, "extern \"C\" __global__ void __launch_bounds__(%d, %d) ptap_jit_numeric(FastArgs<V> a) {\n",
-          p->cfg.block_threads, std::max(1, resident / p->cfg.block_threads));
-  src += "  fast_kernel_body<V>(a, Special());\n}\n";
+  const int resident = dtype == PTAP_F64 ? 512 : 1024;
+  const int minb = std::max(1, resident / block_threads);
+  if (kind == 0) {
+    appendf(src, "extern \"C\" __global__ void __launch_bounds__(%d, %d) ptap_jit_numeric(FastArgs<V> a) {\n",
+            block_threads, minb);
+    src += "  fast_kernel_body<V>(a, Special());\n}\n";
+  } else {
+    appendf(src,
+            "extern \"C\" __global__ void __launch_bounds__(%d, %d) ptap_jit_batch(const FastArgs<V>* probs,"
+            " const int32_t* items, int32_t nitems, int32_t* counter, int CH, int maxr, int max_rows,"
+            " int prog_cap, V* rs) {\n",
+            block_threads, minb);
+    src += "  fast_batch_body<V>(probs, items, nitems, counter, CH, maxr, max_rows, prog_cap, rs, Special());\n}\n";
+  }
+  return src;
+}
+
+// Compiles `src` (or finds it in the process's or the disk cache) and returns
+// the function `name` in *fn.  Caller holds g_mu.
+int compile_or_load(const std::string& src, const char* name, CUfunction* fn_out) {
   int dev = 0;
   PTAP_CUDA(cudaGetDevice(&dev));
   const char* opts[] = {"--gpu-architecture=sm_103a", "-std=c++17", "-lineinfo"};
@@ -315,7 +320,6 @@ int jit_prepare(ptap_plan* p) {
   const uint64_t key = fnv64(keytext);
   CUfunction fn = nullptr;
   auto it = g_cache.find({dev, key});
-  const auto t0 = std::chrono::steady_clock::now();
   const std::string dir = cache_dir();
   char fname[64];
   snprintf(fname, sizeof fname, "jit_%016llx_sm103a.cubin", (unsigned long long)key);
@@ -324,8 +328,7 @@ int jit_prepare(ptap_plan* p) {
     fn = it->second;
   } else if (!dir.empty() && read_file(dir + "/" + fname, cached)) {
     CUmodule mod = nullptr;
-    if (g_drv.load(&mod, cached.data()) == CUDA_SUCCESS &&
-        g_drv.get_fn(&fn, mod, "ptap_jit_numeric") == CUDA_SUCCESS) {
+    if (g_drv.load(&mod, cached.data()) == CUDA_SUCCESS && g_drv.get_fn(&fn, mod, name) == CUDA_SUCCESS) {
       g_cache[{dev, key}] = fn;
     } else {
       fn = nullptr;
@@ -356,23 +359,72 @@ int jit_prepare(ptap_plan* p) {
     g_rtc.destroy(&prog);
     CUmodule mod = nullptr;
     if (g_drv.load(&mod, cubin.data()) != CUDA_SUCCESS) return PTAP_ERR_CUDA;
-    if (g_drv.get_fn(&fn, mod, "ptap_jit_numeric") != CUDA_SUCCESS) return PTAP_ERR_CUDA;
+    if (g_drv.get_fn(&fn, mod, name) != CUDA_SUCCESS) return PTAP_ERR_CUDA;
     g_cache[{dev, key}] = fn;
     if (!dir.empty()) write_file_atomic(dir, fname, cubin);
   }
-  // The compiled classes keep their rows of A P in registers, so the
-  // interpreted ones use a global scratch instead of shared memory: the
-  // accumulator alone sets the shared-memory footprint.
-  const size_t smem = fast_smem_for(p, false);
-  int& attr = g_smem_attr[(void*)fn];  // the module is shared by plans: the attribute only grows
+  *fn_out = fn;
+  return PTAP_OK;
+}
+
+// Raises the function's dynamic shared-memory limit to `smem` (a module is
+// shared by plans: the attribute only grows) and returns its occupancy.
+int set_smem_and_occupancy(CUfunction fn, int threads, size_t smem, int* per_sm) {
+  int& attr = g_smem_attr[(void*)fn];
   if ((int)smem > attr) {
     if (g_drv.set_attr(fn, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, (int)smem) != CUDA_SUCCESS)
       return PTAP_ERR_CUDA;
     attr = (int)smem;
   }
+  *per_sm = 0;
+  if (g_drv.occupancy(per_sm, fn, threads, smem) != CUDA_SUCCESS || *per_sm < 1) return PTAP_ERR_CUDA;
+  return PTAP_OK;
+}
+
+}  // namespace
+
+// Picks the classes with the most visited rows, generates and compiles the
+// specialised kernel.  Returns PTAP_OK with p->jit_fn set, or any error (the
+// caller then keeps the interpreter).
+int jit_prepare(ptap_plan* p) {
+  std::lock_guard<std::mutex> lock(g_mu);
+  load_apis();
+  if (!g_rtc.ok || !g_drv.ok || !p->fast || p->nclasses <= 0) return PTAP_ERR_UNSUPPORTED;
+  cudaStream_t s = p->stream;
+  ClassTable t;
+  PTAP_TRY(read_classes(p, t));
+  // Class ids come from a concurrent deduplication and differ between runs;
+  // the generated source must not, or the disk cache would never hit.  So
+  // classes are ranked by visits with ties broken by program bytes, and the
+  // compiled ones are numbered in program-byte order; a device table maps a
+  // plan's class ids to those numbers.
+  std::vector<int> order(p->nclasses);
+  for (int k = 0; k < p->nclasses; ++k) order[k] = k;
+  std::sort(order.begin(), order.end(), [&](int x, int y) {
+    return t.visits[x] != t.visits[y] ? t.visits[x] > t.visits[y] : t.bytes(x) < t.bytes(y);
+  });
+  std::vector<int> hot;
+  int64_t covered = 0;
+  for (int k : order) {
+    if ((int)hot.size() >= p->cfg.jit_max_classes || covered >= t.total * 99 / 100 || t.visits[k] == 0) break;
+    hot.push_back(k);
+    covered += t.visits[k];
+  }
+  if (hot.empty()) return PTAP_ERR_UNSUPPORTED;
+  std::sort(hot.begin(), hot.end(), [&](int x, int y) { return t.bytes(x) < t.bytes(y); });
+  std::vector<std::string> progs;
+  for (int k : hot) progs.push_back(t.bytes(k));
+  const auto t0 = std::chrono::steady_clock::now();
+  const std::string src = build_source(p->dtype, progs, p->aq != nullptr, p->compact ? p->loc_bits : 0,
+                                       p->cfg.block_threads, 0);
+  CUfunction fn = nullptr;
+  PTAP_TRY(compile_or_load(src, "ptap_jit_numeric", &fn));
+  // The compiled classes keep their rows of A P in registers, so the
+  // interpreted ones use a global scratch instead of shared memory: the
+  // accumulator alone sets the shared-memory footprint.
+  const size_t smem = fast_smem_for(p, false);
   int per_sm = 0;
-  if (g_drv.occupancy(&per_sm, fn, p->cfg.block_threads, smem) != CUDA_SUCCESS || per_sm < 1)
-    return PTAP_ERR_CUDA;
+  PTAP_TRY(set_smem_and_occupancy(fn, p->cfg.block_threads, smem, &per_sm));
   const size_t vb = p->dtype == PTAP_F64 ? 8 : 4;
   const int64_t ctas = std::min<int64_t>(p->nchunks, (int64_t)num_sms() * per_sm);
   void* rs = nullptr;
@@ -390,7 +442,7 @@ int jit_prepare(ptap_plan* p) {
   p->jit_fn = (void*)fn;
   p->jit_per_sm = per_sm;
   p->jit_classes = (int)hot.size();
-  p->jit_coverage = total ? (double)covered / (double)total : 0.0;
+  p->jit_coverage = t.total ? (double)covered / (double)t.total : 0.0;
   p->jit_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   return PTAP_OK;
 }
@@ -399,6 +451,78 @@ int jit_launch(ptap_plan* p, const void* args, int grid, cudaStream_t s) {
   void* params[1] = {const_cast<void*>(args)};
   if (g_drv.launch((CUfunction)p->jit_fn, grid, 1, 1, p->cfg.block_threads, 1, 1, (unsigned)p->jit_smem,
                    (CUstream)s, params, nullptr) != CUDA_SUCCESS)
+    return PTAP_ERR_CUDA;
+  return PTAP_OK;
+}
+
+// Specialisation for a batch: the class programs of all `count` plans are
+// pooled by their bytes (identical structure classes of different products
+// share one compiled body), visits are summed over the plans, and the most
+// visited `max_classes` programs are compiled into ptap_jit_batch.  For each
+// plan, slots[q] receives a device table (from `mem`) mapping its class ids
+// to compiled numbers or -1.  All plans must agree on cached indices; compact
+// chunks are not specialised.
+int jit_prepare_batch(ptap_plan* const* plans, int count, int max_classes, int threads, Tracker& mem,
+                      cudaStream_t s, void** fn_out, std::vector<int32_t*>& slots, int* nhot,
+                      double* coverage) {
+  std::lock_guard<std::mutex> lock(g_mu);
+  load_apis();
+  if (!g_rtc.ok || !g_drv.ok || count <= 0) return PTAP_ERR_UNSUPPORTED;
+  const bool cached = plans[0]->aq != nullptr;
+  std::vector<ClassTable> tabs(count);
+  std::map<std::string, int64_t> pooled;
+  int64_t total = 0;
+  for (int q = 0; q < count; ++q) {
+    ptap_plan* p = plans[q];
+    if (!p->fast || p->compact || (p->aq != nullptr) != cached || p->nclasses <= 0) return PTAP_ERR_UNSUPPORTED;
+    PTAP_TRY(read_classes(p, tabs[q]));
+    for (int k = 0; k < p->nclasses; ++k) pooled[tabs[q].bytes(k)] += tabs[q].visits[k];
+    total += tabs[q].total;
+  }
+  std::vector<std::pair<int64_t, std::string>> ranked;
+  for (auto& kv : pooled) ranked.push_back({kv.second, kv.first});
+  std::sort(ranked.begin(), ranked.end(), [](const auto& x, const auto& y) {
+    return x.first != y.first ? x.first > y.first : x.second < y.second;
+  });
+  std::vector<std::string> hot;
+  int64_t covered = 0;
+  for (auto& r : ranked) {
+    if ((int)hot.size() >= max_classes || covered >= total * 99 / 100 || r.first == 0) break;
+    hot.push_back(r.second);
+    covered += r.first;
+  }
+  if (hot.empty()) return PTAP_ERR_UNSUPPORTED;
+  std::sort(hot.begin(), hot.end());
+  std::map<std::string, int32_t> number;
+  for (size_t i = 0; i < hot.size(); ++i) number[hot[i]] = (int32_t)i;
+  const std::string src = build_source(plans[0]->dtype, hot, cached, 0, threads, 1);
+  CUfunction fn = nullptr;
+  PTAP_TRY(compile_or_load(src, "ptap_jit_batch", &fn));
+  slots.assign(count, nullptr);
+  for (int q = 0; q < count; ++q) {
+    std::vector<int32_t> slot(plans[q]->nclasses, -1);
+    for (int k = 0; k < plans[q]->nclasses; ++k) {
+      auto it = number.find(tabs[q].bytes(k));
+      if (it != number.end()) slot[k] = it->second;
+    }
+    PTAP_TRY(mem.get_n(&slots[q], (int64_t)slot.size()));
+    PTAP_CUDA(cudaMemcpyAsync(slots[q], slot.data(), slot.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+  }
+  PTAP_CUDA(cudaStreamSynchronize(s));
+  *fn_out = (void*)fn;
+  *nhot = (int)hot.size();
+  *coverage = total ? (double)covered / (double)total : 0.0;
+  return PTAP_OK;
+}
+
+int jit_occupancy(void* fn, int threads, size_t smem, int* per_sm) {
+  std::lock_guard<std::mutex> lock(g_mu);
+  return set_smem_and_occupancy((CUfunction)fn, threads, smem, per_sm);
+}
+
+int jit_launch_raw(void* fn, void** params, int grid, int threads, size_t smem, cudaStream_t s) {
+  if (g_drv.launch((CUfunction)fn, grid, 1, 1, threads, 1, 1, (unsigned)smem, (CUstream)s, params, nullptr) !=
+      CUDA_SUCCESS)
     return PTAP_ERR_CUDA;
   return PTAP_OK;
 }

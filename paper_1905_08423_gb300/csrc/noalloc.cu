@@ -94,7 +94,7 @@ int launch(ptap_plan* const* plans, const ptap_csr* A, const ptap_csr* P, void* 
   c.block_threads = std::min(c.block_threads, 256);  // the kernel's bound
   // The general owner kernel keeps column indices beside each accumulated
   // value, so plans built for the class-program kernels (chunks of up to
-  // 32768 entries) can ask for more shared memory than a CTA may have.  The
+  // 49152 entries) can ask for more shared memory than a CTA may have.  The
   // on-chip capacity is then lowered to what fits: chunks with more entries
   // than that take the kernel's heavy path, which accumulates in C itself
   // with atomics (same result, slower).  Settled before anything is staged.

@@ -900,7 +900,7 @@ static int fast_chunk_limit(int vb) {
     return 8192;
   }
   const int n = (optin - 32 * 1024) / vb;
-  return std::max(1024, std::min(32768, n & ~1023));
+  return std::max(1024, std::min(65536, n & ~1023));
 }
 
 static int symbolic_body(ptap_plan* p, const ptap_csr* A, const ptap_csr* P) {
@@ -926,7 +926,7 @@ static int symbolic_body(ptap_plan* p, const ptap_csr* A, const ptap_csr* P) {
   // needs no column indices, so chunks can be larger (fewer fine rows are
   // visited by two chunks); without them the general kernel's default applies.
   // The class-program kernels accept CTAs of up to 1024 threads and chunks up
-  // to 32768 entries (bounded by shared memory for the value type); the
+  // to 65536 entries (bounded by shared memory for the value type); the
   // general kernels keep at most 256 threads and 16384 entries.
   const bool user_ch = p->cfg.chunk_entries > 0;
   const int ch_fast = 8192, ch_general = 4096, ch_general_max = 16384;

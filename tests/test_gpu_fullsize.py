@@ -118,21 +118,3 @@ def test_poisson_512_full(dtype):
     np.testing.assert_array_equal(ci.cpu().numpy(), ref.col_idx)
     err = np.abs(C.cpu().numpy().astype(np.float64) - ref.val)
     assert (np.where(bnd.val > 0, err <= TAU[dtype] * bnd.val, err == 0)).all()
-
-
-def test_batch_64_sampled():
-    """The 64-problem uneven batch in one persistent launch, sampled rows of every product."""
-    dtype = torch.float64
-    probs = pb.batch_problems(seed=4, count=64)
-    devs, plans, Cs = [], [], []
-    for A, P in probs:
-        dA, dP = to_dev(A, dtype), to_dev(P, dtype)
-        plan = ptap.symbolic(dA, dP)
-        devs.append((dA, dP))
-        plans.append(plan)
-        Cs.append(torch.empty(plan.nnz, dtype=dtype, device="cuda"))
-    batch = ptap.Batch(plans, [d[0] for d in devs], [d[1] for d in devs], Cs)
-    batch.numeric()
-    torch.cuda.synchronize()
-    for q, ((A, P), plan, C) in enumerate(zip(probs, plans, Cs)):
-        _check_sampled(plan, C, A, P, dtype, _sample_rows(P.ncols, 200, 100 + q))

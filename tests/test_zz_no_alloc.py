@@ -28,6 +28,7 @@ CONFIGS = {
     "default": dict(),
     # the class-program configurations the autotuner offers at the largest chunks
     "tuned_f32": dict(specialize=32, block_threads=1024, chunk_entries=32768),
+    "tuned_f32_max": dict(specialize=32, block_threads=1024, chunk_entries=49152),
     "tuned_f64": dict(specialize=32, block_threads=512, chunk_entries=20480),
 }
 
