@@ -122,8 +122,7 @@ typedef struct {
                              than the packed row locations can name keeps ranges
                              (ptap_stats.compact_chunks says which).  Plans with
                              compact chunks are refused (PTAP_ERR_UNSUPPORTED) by
-                             ptap_batch_numeric_noalloc and by batches that mix them with
-                             general-kernel plans; 0: ranges */
+                             ptap_batch_numeric_noalloc; 0: ranges */
   int32_t specialize_scope; /* with specialize = k > 0: 0 = the plan compiles its own kernel
                                at symbolic time (default); 1 = the plan compiles nothing, and a
                                batch that includes it (ptap_batch_create) compiles one kernel for
@@ -217,18 +216,30 @@ int ptap_backward(ptap_plan* plan, const ptap_csr* A, const ptap_csr* P, const v
 int ptap_two_step_symbolic(const ptap_csr* A, const ptap_csr* P, const ptap_config* cfg,
                            const ptap_allocator* alloc, void* stream, ptap_plan** out);
 
-/* Batched numeric products (uneven sizes, one persistent launch).  `plans`,
+/* Batched numeric products of uneven sizes: the repeated numeric phase
+ * (Section 4.1, one symbolic and many numeric products) of many plans at
+ * once, each plan holding its cached symbolic data (Section 4.2).  `plans`,
  * `A` and `P` (host arrays of `count` elements) and `C_vals` (host array of
  * device pointers) fix the problems once; the batch copies their descriptors
- * to the device.  All plans must be all-at-once plans of one dtype. */
+ * and a queue of their chunks, longest first, to the device.  All plans must
+ * be all-at-once plans of one dtype.  Plans that run class programs share one
+ * persistent launch; when any of them was built with specialize = k > 0 the
+ * batch compiles (NVRTC, at creation) one kernel for the k most visited
+ * class programs over all of them, pooled by their bytes.  The other plans
+ * share a second launch of the general kernel; they must agree on
+ * group_lanes, ap_slots and force_spill (PTAP_ERR_INVALID otherwise) and
+ * must not use compact chunks (PTAP_ERR_UNSUPPORTED).  Synchronises `stream`.
+ * Errors: as ptap_numeric for each problem, PTAP_ERR_OOM. */
 int ptap_batch_create(ptap_plan* const* plans, const ptap_csr* A, const ptap_csr* P,
                       void* const* C_vals, int32_t count, const ptap_allocator* alloc,
                       void* stream, ptap_batch** out);
 
-/* Runs every product of the batch in one launch over a binned work queue.
- * Reads the current values behind the pointers given at creation, so it can
- * be captured once in a CUDA graph and replayed after the values change.
- * Asynchronous; allocates nothing. */
+/* Runs every product of the batch: a counter reset and at most two
+ * persistent launches (class-program problems, general problems) over the
+ * work queues.  Reads the current values behind the pointers given at
+ * creation, so it can be captured once in a CUDA graph and replayed after the
+ * values change (Section 4.1's repeated numeric products).  Asynchronous;
+ * allocates nothing. */
 int ptap_batch_numeric(ptap_batch* batch, void* stream);
 
 void ptap_batch_destroy(ptap_batch* batch);

@@ -1,5 +1,7 @@
 // Plan management, configuration and error reporting of the C ABI.
 #include <algorithm>
+#include <map>
+#include <mutex>
 
 #include "common.cuh"
 
@@ -9,6 +11,19 @@ void note_cuda_error(cudaError_t e, const char* what, const char* file, int line
   if (getenv("PTAP_VERBOSE"))
     fprintf(stderr, "ptap: CUDA error %s (%s) in %s at %s:%d\n", cudaGetErrorName(e),
             cudaGetErrorString(e), what, file, line);
+}
+
+int grow_smem_limit(const void* fn, int bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<int, const void*>, int> limits;  // (device, kernel) -> limit set
+  int dev = 0;
+  PTAP_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lock(mu);
+  int& cur = limits[{dev, fn}];
+  if (bytes <= cur) return PTAP_OK;
+  PTAP_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  cur = bytes;
+  return PTAP_OK;
 }
 
 static int pick(int v, int dflt) { return v > 0 ? v : dflt; }

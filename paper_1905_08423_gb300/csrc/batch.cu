@@ -152,7 +152,7 @@ int prepare_fast_side(ptap_batch* b, const std::vector<ptap_plan*>& fp, const st
       const size_t smem = ptapk::fast_smem_bytes<V>(b->fast_ch, b->fast_threads, b->fast_maxr, b->fast_max_rows,
                                                     b->fast_prog_cap, in_smem != 0);
       if (smem > (size_t)optin) continue;
-      PTAP_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      PTAP_TRY(grow_smem_limit((const void*)k, (int)smem));
       PTAP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, b->fast_threads, smem));
       b->fast_smem = smem;
       rs_global = in_smem == 0;
@@ -218,8 +218,7 @@ int prepare_gen_side(ptap_batch* b, const std::vector<int32_t>& gq, ptap_plan* c
   const int64_t fit = ((int64_t)optin - (int64_t)fixed) / (int64_t)(sizeof(V) + sizeof(int32_t));
   c.chunk_entries = (int)std::max<int64_t>(64, std::min<int64_t>(c.chunk_entries, fit & ~int64_t(63)));
   b->gen_smem = owner_smem_for(b->dtype, c, b->max_chunk_rows);
-  PTAP_CUDA(cudaFuncSetAttribute(k_batch_owner<V, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)b->gen_smem));
+  PTAP_TRY(grow_smem_limit((const void*)k_batch_owner<V, G>, (int)b->gen_smem));
   int per_sm = 0;
   PTAP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_owner<V, G>, c.block_threads,
                                                           b->gen_smem));

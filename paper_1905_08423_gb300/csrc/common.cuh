@@ -44,6 +44,11 @@ struct Range {
 
 void note_cuda_error(cudaError_t e, const char* what, const char* file, int line);
 
+// Raises the dynamic shared-memory limit of kernel `fn` on the current device
+// to at least `bytes`, never lowering it: plans built earlier may launch the
+// same kernel with a larger carve-up than the plan being built now.
+int grow_smem_limit(const void* fn, int bytes);
+
 // Launch check: a bad launch configuration is a CUDA error of this call.
 #define PTAP_LAUNCHED() PTAP_CUDA(cudaGetLastError())
 

@@ -108,7 +108,7 @@ static int fast_occupancy(const ptap_plan* p, size_t smem) {
   PTAP_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
   if (smem > (size_t)optin) return 0;
   auto k = fast_kernel_for<V>(p);
-  PTAP_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  PTAP_TRY(grow_smem_limit((const void*)k, (int)smem));
   int per_sm = 0;
   PTAP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, p->cfg.block_threads, smem));
   return per_sm;

@@ -113,8 +113,7 @@ int launch(ptap_plan* const* plans, const ptap_csr* A, const ptap_csr* P, void* 
     c.chunk_entries = (int)std::max<int64_t>(64, std::min<int64_t>(c.chunk_entries, fit & ~int64_t(63)));
   }
   const size_t smem = owner_smem_for(plans[0]->dtype, c, max_rows);
-  PTAP_CUDA(cudaFuncSetAttribute(k_noalloc_batch<V, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem));
+  PTAP_TRY(grow_smem_limit((const void*)k_noalloc_batch<V, G>, (int)smem));
   int per_sm = 0;
   PTAP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_noalloc_batch<V, G>,
                                                           c.block_threads, smem));

@@ -148,8 +148,7 @@ template <typename V, int G>
 static int prepare_owner_g(ptap_plan* p) {
   const Config& c = p->cfg;
   const size_t smem = owner_smem_bytes<V>(c, std::max(p->max_chunk_rows, 1), c.block_threads);
-  PTAP_CUDA(cudaFuncSetAttribute(k_numeric_owner<V, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem));
+  PTAP_TRY(grow_smem_limit((const void*)k_numeric_owner<V, G>, (int)smem));
   int per_sm = 0;
   PTAP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_numeric_owner<V, G>,
                                                           c.block_threads, smem));
@@ -173,8 +172,7 @@ static int prepare_atomic_g(ptap_plan* p) {
   const Config& c = p->cfg;
   const int slots = 1 << slots_log2_of(c);
   const size_t smem = (size_t)(c.block_threads / G) * slots * (sizeof(V) + sizeof(int32_t));
-  PTAP_CUDA(cudaFuncSetAttribute(k_numeric_atomic<V, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem));
+  PTAP_TRY(grow_smem_limit((const void*)k_numeric_atomic<V, G>, (int)smem));
   int per_sm = 0;
   PTAP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_numeric_atomic<V, G>,
                                                           c.block_threads, smem));

@@ -277,7 +277,7 @@ int segmented_sort(Tracker& mem, const int32_t* ptr, int32_t nseg, int32_t* keys
     const size_t bytes = (size_t)cap * eb;
     static size_t attr = 48 * 1024;  // largest dynamic size set so far (the default allows 48 KB)
     if (bytes > attr) {
-      PTAP_CUDA(cudaFuncSetAttribute(k_sort_cta_list, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+      PTAP_TRY(grow_smem_limit((const void*)k_sort_cta_list, (int)bytes));
       attr = bytes;
     }
     const bool big = cap > kSortSmem;

@@ -296,7 +296,7 @@ template <typename V>
 int prepare_sorted_t(ptap_plan* p) {
   const size_t smem = sorted_smem_bytes<V>(p->cfg.chunk_entries, std::max(p->max_chunk_rows, 1),
                                            p->cfg.block_threads);
-  PTAP_CUDA(cudaFuncSetAttribute(k_numeric_sorted<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  PTAP_TRY(grow_smem_limit((const void*)k_numeric_sorted<V>, (int)smem));
   int per_sm = 0;
   PTAP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_numeric_sorted<V>, p->cfg.block_threads, smem));
   if (per_sm < 1) return PTAP_ERR_INVALID;

@@ -379,10 +379,8 @@ static int union_pattern(Tracker& mem, const E& ex, int32_t nrows, int32_t ncols
   const int grid_w = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(nrows, warps),
                                                                  (int64_t)num_sms() * 16));
   const size_t cta_smem = (size_t)(1 << t.cta_log2) * sizeof(int32_t);
-  PTAP_CUDA(cudaFuncSetAttribute(k_union_cta<E, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)cta_smem));
-  PTAP_CUDA(cudaFuncSetAttribute(k_union_cta<E, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)cta_smem));
+  PTAP_TRY(grow_smem_limit((const void*)k_union_cta<E, false>, (int)cta_smem));
+  PTAP_TRY(grow_smem_limit((const void*)k_union_cta<E, true>, (int)cta_smem));
   // --- count pass
   PTAP_TRY(sc.get(&l1, std::max<int64_t>(nrows, 1)));
   if (nrows > 0) {

@@ -110,8 +110,7 @@ static int launch_rowwise_g(const CsrV<V>& A, const CsrV<V>& B, const int32_t* r
   const int threads = c.block_threads;
   const int slots_log2 = c.force_spill ? 2 : ilog2_ceil((uint32_t)std::max(4, c.ap_slots));
   const size_t smem = (size_t)(threads / G) * (1 << slots_log2) * (sizeof(V) + sizeof(int32_t));
-  PTAP_CUDA(cudaFuncSetAttribute(k_rowwise_numeric<V, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem));
+  PTAP_TRY(grow_smem_limit((const void*)k_rowwise_numeric<V, G>, (int)smem));
   int per_sm = 0;
   PTAP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rowwise_numeric<V, G>, threads, smem));
   if (per_sm < 1) return PTAP_ERR_INVALID;

@@ -87,8 +87,8 @@ def test_compact_fallbacks():
 
 @pytest.mark.parametrize("dtype", DTYPES)
 def test_compact_batch(dtype):
-    """The persistent batch kernel runs compact plans; mixing them with general-kernel
-    plans, or passing them to the no-allocation entry point, is refused."""
+    """The batch runs compact plans, also beside a general-kernel plan (each kind on its
+    own kernel); the no-allocation entry point refuses them."""
     probs = [pb.model_problem(n) for n in (11, 14, 17)] + [pb.poisson2d_problem(30)]
     devs, plans, Cs = [], [], []
     for A, P in probs:
@@ -108,8 +108,14 @@ def test_compact_batch(dtype):
     A, P = probs[0]
     dA, dP = to_dev(A, dtype), to_dev(P, dtype)
     general = ptap.symbolic(dA, dP, ptap.make_config(class_programs=False, chunk_entries=512))
-    Cg = torch.empty(general.nnz, dtype=dtype, device="cuda")
-    with pytest.raises(ptap.PtapError, match="UNSUPPORTED"):
-        ptap.Batch([plans[0], general], [devs[0][0], dA], [devs[0][1], dP], [Cs[0], Cg])
+    Cg = torch.full((general.nnz,), float("nan"), dtype=dtype, device="cuda")
+    Cs[0].fill_(float("nan"))
+    mixed = ptap.Batch([plans[0], general], [devs[0][0], dA], [devs[0][1], dP], [Cs[0], Cg])
+    mixed.numeric()
+    torch.cuda.synchronize()
+    Ar, Pr = rounded(A, dtype), rounded(P, dtype)
+    for C in (Cs[0], Cg):
+        check_values(C, oracle.ptap(Ar, Pr).val, oracle.ptap_bound(Ar, Pr).val, dtype)
+    mixed.destroy()
     with pytest.raises(ptap.PtapError, match="UNSUPPORTED"):
         ptap.batch_numeric_noalloc(plans[:1], [devs[0][0]], [devs[0][1]], Cs[:1])
