@@ -130,7 +130,10 @@ typedef struct {
   int32_t reserved[2];
 } ptap_config;
 
-/* Statistics of a plan (host struct filled by ptap_plan_stats). */
+/* Statistics of a plan (host struct filled by ptap_plan_stats).  The byte
+ * counts are the quantity the paper compares between algorithms: memory that
+ * includes the storage of C (Section 4.1, the "Mem" columns of Tables 1, 3
+ * and 7). */
 typedef struct {
   int32_t n, m;
   int64_t nnz_a, nnz_p, nnz_c;
@@ -169,9 +172,12 @@ typedef struct ptap_batch ptap_batch;
 int ptap_symbolic(const ptap_csr* A, const ptap_csr* P, const ptap_config* cfg,
                   const ptap_allocator* alloc, void* stream, ptap_plan** out);
 
-/* Pattern of C held by the plan: *m rows, *nnz entries, device pointers to
- * row_ptr (m+1) and col_idx (nnz), owned by the plan and valid until
- * ptap_plan_destroy.  Any output pointer may be NULL. */
+/* Pattern of C held by the plan: the preallocated structure of C that the
+ * symbolic phase determines without floating point (Section 2, after Alg. 2;
+ * Section 3, Alg. 7, where the counts preallocate C).  *m rows, *nnz entries,
+ * device pointers to row_ptr (m+1) and col_idx (nnz, ascending per row),
+ * owned by the plan and valid until ptap_plan_destroy.  Any output pointer
+ * may be NULL.  Errors: PTAP_ERR_INVALID for a NULL plan. */
 int ptap_plan_pattern(const ptap_plan* plan, int32_t* m, int64_t* nnz,
                       const int32_t** row_ptr, const int32_t** col_idx);
 
@@ -242,16 +248,23 @@ int ptap_batch_create(ptap_plan* const* plans, const ptap_csr* A, const ptap_csr
  * allocates nothing. */
 int ptap_batch_numeric(ptap_batch* batch, void* stream);
 
+/* Frees the batch's descriptors and queues (not the plans, which the caller
+ * still owns and must outlive the batch).  NULL is a no-op. */
 void ptap_batch_destroy(ptap_batch* batch);
 
-/* Statistics of a plan; see ptap_stats. */
+/* Statistics of a plan (Section 4.1, "Mem"; see ptap_stats), written into
+ * the caller's host struct.  Errors: PTAP_ERR_INVALID for NULL arguments. */
 int ptap_plan_stats(const ptap_plan* plan, ptap_stats* out);
 
 /* Reads and clears the plan's device status word (synchronises `stream`):
- * PTAP_OK, or the PTAP_ERR_* code a kernel of this plan recorded. */
+ * PTAP_OK, or the PTAP_ERR_* code a kernel of this plan recorded (a device
+ * table that ran out of space, an input that did not match the pattern).
+ * The paper has no counterpart: its hash tables grow on the host. */
 int ptap_plan_check(ptap_plan* plan, void* stream);
 
-/* Frees everything the plan holds (stream-ordered on the plan's stream). */
+/* Frees everything the plan holds: C's pattern, the schedule and the cached
+ * symbolic data of Section 4.2 (stream-ordered on the plan's stream).  NULL is
+ * a no-op. */
 void ptap_plan_destroy(ptap_plan* plan);
 
 /* Static description of an error code. */
