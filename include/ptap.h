@@ -273,6 +273,27 @@ const char* ptap_error_string(int code);
 /* Version of this library as major*10000 + minor*100 + patch. */
 int ptap_version(void);
 
+/* ---- value movement of the row-partitioned product ----------------------
+ * With A's and P's fine rows split into blocks over processes (Section 2,
+ * Eq. 1-3), a process gathers the rows of P that its block of A references
+ * but others own (P~_r, one sparse exchange per phase, Section 2, Alg. 2 and
+ * 4) and sends the outer-product contributions it made to coarse rows that
+ * others own (C_s, Section 3, Alg. 7-8) to their owners, who add them.  The
+ * index lists are fixed by the symbolic phase; these calls move the values
+ * of each numeric phase.  All pointers are device pointers; values have the
+ * given dtype.  Asynchronous on `stream`; allocate nothing.
+ *
+ * ptap_gather: out[e] = src[src_idx[e]] for e < n (packing a send buffer).
+ * ptap_scatter_add: dst[dst_idx[e]] += src[src_idx[e]] (src_idx NULL: src[e])
+ * for e < n; the positions dst_idx[0..n) must be distinct within one call
+ * (the entries are added without atomics).
+ * Errors: PTAP_ERR_INVALID for a negative n, a bad dtype or a NULL pointer
+ * with n > 0; PTAP_ERR_CUDA for a launch failure. */
+int ptap_gather(const void* src, const int32_t* src_idx, int64_t n, int32_t dtype, void* out,
+                void* stream);
+int ptap_scatter_add(const void* src, const int32_t* src_idx, const int32_t* dst_idx, int64_t n,
+                     int32_t dtype, void* dst, void* stream);
+
 /* ---- batched numeric products that allocate nothing ---------------------
  * The paper has no counterpart to this entry point.  It serves callers that
  * cannot allocate device memory when the products run: solvers that reserve

@@ -6,6 +6,7 @@
 #include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <cstdio>
 #include <cstring>
 #include <unordered_map>

@@ -82,7 +82,8 @@ _PP = _c.POINTER(_c.c_void_p)
 SYMBOLS = ["ptap_symbolic", "ptap_plan_pattern", "ptap_numeric", "ptap_backward",
            "ptap_two_step_symbolic", "ptap_batch_create", "ptap_batch_numeric",
            "ptap_batch_destroy", "ptap_plan_stats", "ptap_plan_check", "ptap_plan_destroy",
-           "ptap_error_string", "ptap_version"]
+           "ptap_error_string", "ptap_version", "ptap_gather", "ptap_scatter_add",
+           "ptap_numeric_host", "ptap_batch_numeric_noalloc"]
 
 
 def lib_path() -> str:
@@ -117,6 +118,8 @@ def _lib():
         L.ptap_error_string.argtypes = [_c.c_int]
         L.ptap_error_string.restype = _c.c_char_p
         L.ptap_version.argtypes = []
+        L.ptap_gather.argtypes = [_VP, _VP, _c.c_int64, _c.c_int32, _VP, _VP]
+        L.ptap_scatter_add.argtypes = [_VP, _VP, _VP, _c.c_int64, _c.c_int32, _VP, _VP]
         missing = [name for name in SYMBOLS if not hasattr(L, name)]
         if missing:
             raise RuntimeError(f"{path} lacks {missing}")
@@ -437,3 +440,41 @@ def batch_numeric_noalloc(plans, As, Ps, Cs, stream=None):
     cc = (_VP * n)(*[c.data_ptr() for c in Cs])
     _check(f(hp, ca, cp, cc, n, _stream(stream)), "ptap_batch_numeric_noalloc")
 
+
+
+def _vcode(t: torch.Tensor) -> int:
+    if t.dtype == torch.float64:
+        return F64
+    if t.dtype == torch.float32:
+        return F32
+    raise TypeError(f"unsupported value dtype {t.dtype}")
+
+
+def gather(src: torch.Tensor, idx: torch.Tensor, out: torch.Tensor | None = None, stream=None):
+    """ptap_gather: out[e] = src[idx[e]] (packing exchanged values of the row partition)."""
+    assert src.is_cuda and src.is_contiguous() and idx.is_cuda and idx.dtype == torch.int32
+    idx = idx.contiguous()
+    if out is None:
+        out = torch.empty(idx.numel(), dtype=src.dtype, device=src.device)
+    assert out.is_contiguous() and out.dtype == src.dtype and out.numel() >= idx.numel()
+    _check(_lib().ptap_gather(src.data_ptr(), idx.data_ptr(), idx.numel(), _vcode(src), out.data_ptr(),
+                              _stream(stream)), "ptap_gather")
+    return out
+
+
+def scatter_add(dst: torch.Tensor, dst_idx: torch.Tensor, src: torch.Tensor,
+                src_idx: torch.Tensor | None = None, stream=None):
+    """ptap_scatter_add: dst[dst_idx[e]] += src[src_idx[e] or e] (distinct dst_idx in one call)."""
+    assert dst.is_cuda and dst.is_contiguous() and src.is_cuda and src.is_contiguous()
+    assert src.dtype == dst.dtype and dst_idx.dtype == torch.int32
+    n = dst_idx.numel()
+    if src_idx is not None:
+        assert src_idx.dtype == torch.int32 and src_idx.numel() == n
+        src_idx = src_idx.contiguous()
+    else:
+        assert src.numel() >= n
+    dst_idx = dst_idx.contiguous()
+    _check(_lib().ptap_scatter_add(src.data_ptr(), src_idx.data_ptr() if src_idx is not None else None,
+                                   dst_idx.data_ptr(), n, _vcode(dst), dst.data_ptr(), _stream(stream)),
+           "ptap_scatter_add")
+    return dst

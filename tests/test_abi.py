@@ -112,3 +112,20 @@ def test_binding_structs_mirror_the_header():
     assert cfg.compact_chunks == 1
     assert ptap.make_config(compact_chunks=32).compact_chunks == 32
     assert ptap.make_config().compact_chunks == 0
+
+
+def test_exchange_calls_validate_on_host(lib):
+    """ptap_gather / ptap_scatter_add reject bad sizes, dtypes and NULL pointers before
+    any device work, and accept n = 0 as a no-op."""
+    g, s = lib.ptap_gather, lib.ptap_scatter_add
+    g.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p,
+                  ctypes.c_void_p]
+    s.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
+                  ctypes.c_void_p, ctypes.c_void_p]
+    assert g(0x1000, 0x2000, -1, 0, 0x3000, None) == 1
+    assert g(0x1000, 0x2000, 4, 7, 0x3000, None) == 1
+    assert g(None, 0x2000, 4, 0, 0x3000, None) == 1
+    assert g(None, None, 0, 0, None, None) == 0
+    assert s(0x1000, None, None, 4, 1, 0x3000, None) == 1
+    assert s(0x1000, None, 0x2000, -2, 1, 0x3000, None) == 1
+    assert s(None, None, None, 0, 1, None, None) == 0
