@@ -175,27 +175,38 @@ __device__ int compute_sig(const SigGeom& g, int32_t I, uint8_t* sig, int32_t* c
   }
   const int ssec = tsec + 8 * na;
   const int tcur = ssec + 8 * r;
-  // positions in the rows of C (sigma): every (s, t) pair searches its C row
-  // in parallel (the rows are short and shared by neighbouring fine rows, so
-  // the searches mostly hit L1)
+  // positions in the rows of C (sigma).  For each entry s of P(I,:) the warp
+  // loads the columns of C row i_s, 32 at a time (one coalesced load), and
+  // ranks every slot's column keys[t] among them with ballots: its position
+  // is the number of smaller columns, and it must be present.  No dependent
+  // chain of loads, unlike one binary search per (s, t).
   bool too_long = false;
-  for (int32_t e = lane; e < pI * r; e += 32) {
-    const int32_t s = e / r, t = e - s * r;
+  const int32_t mykey = lane < r ? keys[lane] : 0;
+  for (int32_t s = 0; s < pI; ++s) {
     const int32_t i = g.P.ci[p0 + s];
-    const int32_t c0 = g.C.rp[i], L = g.C.rp[i + 1] - c0;
+    const int32_t c0 = g.C.rp[i], L = g.C.rp[i + 1] - c0;  // the same for every lane
     if (L > 255) {
       too_long = true;
-      continue;
+      break;
     }
-    const int32_t kt = keys[t];
-    int32_t lo = 0, hi = L;
-    while (lo < hi) {
-      const int32_t mid = (lo + hi) >> 1;
-      if (g.C.ci[c0 + mid] < kt) lo = mid + 1;
-      else hi = mid;
+    int32_t pos = 0;
+    bool found = false;
+    for (int32_t base = 0; base < L; base += 32) {
+      const int32_t cj = base + lane < L ? g.C.ci[c0 + base + lane] : 0x7fffffff;
+      for (int32_t t = 0; t < r; ++t) {
+        const int32_t kt = __shfl_sync(0xffffffffu, mykey, t);
+        const unsigned lt = __ballot_sync(0xffffffffu, cj < kt);
+        const unsigned eq = __ballot_sync(0xffffffffu, cj == kt);
+        if (lane == t) {
+          pos += __popc(lt);
+          found = found || eq != 0u;
+        }
+      }
     }
-    if (lo >= L || g.C.ci[c0 + lo] != kt) atomicExch(status, PTAP_ERR_PATTERN);
-    sig[ssec + t * 8 + s] = (uint8_t)lo;
+    if (lane < r) {
+      if (!found) atomicExch(status, PTAP_ERR_PATTERN);
+      sig[ssec + lane * 8 + s] = (uint8_t)pos;
+    }
   }
   if (__any_sync(0xffffffffu, too_long)) return -1;
   if (lane == 0) {

@@ -185,10 +185,13 @@ __device__ void warp_emit_sorted(int32_t* keys, int cap, int count, int32_t* tmp
 
 // Tier 0: one warp per row, a private table of 2^cap_log2 slots in shared
 // memory.  Rows whose distinct count exceeds `limit` go to tier 1.
+// With `stash` (count pass only), a row of at most 32 columns also leaves
+// them sorted in stash[32 row ..] and is marked tier 3: the fill pass then
+// copies it instead of expanding the row a second time.
 template <class E, bool FILL>
 __global__ void k_union_warp(E ex, int32_t nrows, int cap_log2, int limit, uint8_t* tier,
                              int32_t* cnt, const int32_t* __restrict__ out_rp, int32_t* out_ci,
-                             int32_t* ovf_list, int32_t* ovf_count) {
+                             int32_t* ovf_list, int32_t* ovf_count, int32_t* stash) {
   extern __shared__ int32_t sm[];
   __shared__ int32_t wcount[32];
   __shared__ int32_t wflag[32];
@@ -217,13 +220,15 @@ __global__ void k_union_warp(E ex, int32_t nrows, int cap_log2, int limit, uint8
     const int count = ((volatile int32_t*)wcount)[w];
     const int ovf = ((volatile int32_t*)wflag)[w];
     if (!FILL) {
+      const bool stashed = stash && !ovf && count <= 32;
+      if (stashed) warp_emit_sorted(keys, cap, count, tmp, stash + (int64_t)row * 32, lane);
       if (lane == 0) {
         if (ovf) {
           tier[row] = 1;
           cnt[row] = 0;
           ovf_list[atomicAdd(ovf_count, 1)] = row;
         } else {
-          tier[row] = 0;
+          tier[row] = stashed ? 3 : 0;
           cnt[row] = count;
         }
       }
@@ -231,6 +236,17 @@ __global__ void k_union_warp(E ex, int32_t nrows, int cap_log2, int limit, uint8
       warp_emit_sorted(keys, cap, count, tmp, out_ci + out_rp[row], lane);
     }
     __syncwarp();
+  }
+}
+
+// Fill pass of the stashed rows: their sorted columns to their place in C.
+__global__ void k_unstash(int32_t nrows, const uint8_t* __restrict__ tier, const int32_t* __restrict__ stash,
+                          const int32_t* __restrict__ out_rp, int32_t* out_ci) {
+  const int warps = blockDim.x >> 5, lane = threadIdx.x & 31;
+  for (int64_t r = (int64_t)blockIdx.x * warps + (threadIdx.x >> 5); r < nrows; r += (int64_t)gridDim.x * warps) {
+    if (tier[r] != 3) continue;
+    const int32_t b = out_rp[r], len = out_rp[r + 1] - b;
+    if (lane < len) out_ci[b + lane] = stash[r * 32 + lane];
   }
 }
 
@@ -381,11 +397,15 @@ static int union_pattern(Tracker& mem, const E& ex, int32_t nrows, int32_t ncols
   const size_t cta_smem = (size_t)(1 << t.cta_log2) * sizeof(int32_t);
   PTAP_TRY(grow_smem_limit((const void*)k_union_cta<E, false>, (int)cta_smem));
   PTAP_TRY(grow_smem_limit((const void*)k_union_cta<E, true>, (int)cta_smem));
-  // --- count pass
+  // --- count pass (rows of at most 32 columns also keep them in a stash, when
+  //     the 128 bytes a row fit: the fill pass then only copies those rows)
   PTAP_TRY(sc.get(&l1, std::max<int64_t>(nrows, 1)));
+  int32_t* stash = nullptr;
+  if (nrows > 0 && (int64_t)nrows * 128 <= ((int64_t)2 << 30) && mem.get_n(&stash, (int64_t)nrows * 32) != PTAP_OK)
+    stash = nullptr;
   if (nrows > 0) {
     k_union_warp<E, false><<<grid_w, threads, warp_smem, s>>>(ex, nrows, t.warp_log2, t.warp_limit,
-                                                               tier, cnt, nullptr, nullptr, l1, ctr);
+                                                               tier, cnt, nullptr, nullptr, l1, ctr, stash);
     PTAP_LAUNCHED();
   }
   int32_t h_ctr[2] = {0, 0};
@@ -432,8 +452,13 @@ static int union_pattern(Tracker& mem, const E& ex, int32_t nrows, int32_t ncols
   // --- fill pass
   if (nrows > 0) {
     k_union_warp<E, true><<<grid_w, threads, warp_smem, s>>>(ex, nrows, t.warp_log2, t.warp_limit,
-                                                              tier, cnt, rp, *ci, nullptr, nullptr);
+                                                              tier, cnt, rp, *ci, nullptr, nullptr, nullptr);
     PTAP_LAUNCHED();
+    if (stash) {
+      k_unstash<<<grid_w, threads, 0, s>>>(nrows, tier, stash, rp, *ci);
+      PTAP_LAUNCHED();
+      mem.put(stash);
+    }
   }
   if (n1 > 0) {
     const int grid = (int)std::min<int64_t>(n1, (int64_t)num_sms() * 4);
