@@ -13,6 +13,13 @@ void note_cuda_error(cudaError_t e, const char* what, const char* file, int line
             cudaGetErrorString(e), what, file, line);
 }
 
+bool profile_enabled() {
+  static const bool on = getenv("PTAP_PROFILE") != nullptr;
+  return on;
+}
+
+void profile_report(const char* name, double ms) { fprintf(stderr, "ptap: %-44s %9.3f ms\n", name, ms); }
+
 int grow_smem_limit(const void* fn, int bytes) {
   static std::mutex mu;
   static std::map<std::pair<int, const void*>, int> limits;  // (device, kernel) -> limit set

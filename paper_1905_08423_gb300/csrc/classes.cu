@@ -175,38 +175,27 @@ __device__ int compute_sig(const SigGeom& g, int32_t I, uint8_t* sig, int32_t* c
   }
   const int ssec = tsec + 8 * na;
   const int tcur = ssec + 8 * r;
-  // positions in the rows of C (sigma).  For each entry s of P(I,:) the warp
-  // loads the columns of C row i_s, 32 at a time (one coalesced load), and
-  // ranks every slot's column keys[t] among them with ballots: its position
-  // is the number of smaller columns, and it must be present.  No dependent
-  // chain of loads, unlike one binary search per (s, t).
+  // positions in the rows of C (sigma): every (s, t) pair searches its C row
+  // in parallel (the rows are short and shared by neighbouring fine rows, so
+  // the searches mostly hit L1)
   bool too_long = false;
-  const int32_t mykey = lane < r ? keys[lane] : 0;
-  for (int32_t s = 0; s < pI; ++s) {
+  for (int32_t e = lane; e < pI * r; e += 32) {
+    const int32_t s = e / r, t = e - s * r;
     const int32_t i = g.P.ci[p0 + s];
-    const int32_t c0 = g.C.rp[i], L = g.C.rp[i + 1] - c0;  // the same for every lane
+    const int32_t c0 = g.C.rp[i], L = g.C.rp[i + 1] - c0;
     if (L > 255) {
       too_long = true;
-      break;
+      continue;
     }
-    int32_t pos = 0;
-    bool found = false;
-    for (int32_t base = 0; base < L; base += 32) {
-      const int32_t cj = base + lane < L ? g.C.ci[c0 + base + lane] : 0x7fffffff;
-      for (int32_t t = 0; t < r; ++t) {
-        const int32_t kt = __shfl_sync(0xffffffffu, mykey, t);
-        const unsigned lt = __ballot_sync(0xffffffffu, cj < kt);
-        const unsigned eq = __ballot_sync(0xffffffffu, cj == kt);
-        if (lane == t) {
-          pos += __popc(lt);
-          found = found || eq != 0u;
-        }
-      }
+    const int32_t kt = keys[t];
+    int32_t lo = 0, hi = L;
+    while (lo < hi) {
+      const int32_t mid = (lo + hi) >> 1;
+      if (g.C.ci[c0 + mid] < kt) lo = mid + 1;
+      else hi = mid;
     }
-    if (lane < r) {
-      if (!found) atomicExch(status, PTAP_ERR_PATTERN);
-      sig[ssec + lane * 8 + s] = (uint8_t)pos;
-    }
+    if (lo >= L || g.C.ci[c0 + lo] != kt) atomicExch(status, PTAP_ERR_PATTERN);
+    sig[ssec + t * 8 + s] = (uint8_t)lo;
   }
   if (__any_sync(0xffffffffu, too_long)) return -1;
   if (lane == 0) {
@@ -573,6 +562,7 @@ int build_classes(ptap_plan* p, const ptap_csr* A, const ptap_csr* P, cudaStream
   c.status = p->status;
   // latency-bound warp-per-row work: fill the SMs (16 CTAs of 4 warps each)
   const int grid = num_sms() * 16;
+  PhaseRange r_build("ptap: class signatures", s);
   k_class_build<<<grid, kSigWarps * 32, 0, s>>>(c);
   PTAP_LAUNCHED();
   int32_t h[5];
@@ -668,7 +658,10 @@ int build_classes(ptap_plan* p, const ptap_csr* A, const ptap_csr* P, cudaStream
   k_visit_keys<<<grid, 256, 0, s>>>(p->chunk_fptr, p->chunk_frows, p->nchunks, row_class, shift,
                                     kBlockBits, rank, keys);
   PTAP_LAUNCHED();
-  PTAP_TRY(segmented_sort(p->mem, p->chunk_fptr, p->nchunks, keys, p->chunk_frows, -1, s));
+  {
+    PhaseRange r_sort("ptap: visit order sort", s);
+    PTAP_TRY(segmented_sort(p->mem, p->chunk_fptr, p->nchunks, keys, p->chunk_frows, -1, s));
+  }
   k_seg_flags<<<grid, 256, 0, s>>>(p->chunk_fptr, p->nchunks, keys, shift, kBlockBits, flag);
   PTAP_LAUNCHED();
   int64_t nseg = 0;

@@ -7,6 +7,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cstdio>
 #include <cstring>
 #include <unordered_map>
@@ -18,11 +19,33 @@ namespace ptap {
 
 // Named range for profilers (NVTX): a timeline shows the library's phases.
 // It costs nothing unless a profiling tool is attached.
+// With PTAP_PROFILE set, the host time of every range (phases end with a
+// stream synchronisation where their results are needed) goes to stderr.
+bool profile_enabled();
+void profile_report(const char* name, double ms);
 struct Range {
-  explicit Range(const char* name) { nvtxRangePushA(name); }
-  ~Range() { nvtxRangePop(); }
+  explicit Range(const char* n) : name(n) {
+    nvtxRangePushA(n);
+    if (profile_enabled()) t0 = std::chrono::steady_clock::now();
+  }
+  ~Range() {
+    nvtxRangePop();
+    if (profile_enabled())
+      profile_report(name, std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count());
+  }
+  const char* name;
+  std::chrono::steady_clock::time_point t0{};
   Range(const Range&) = delete;
   Range& operator=(const Range&) = delete;
+};
+
+// A range whose profiled time includes the work it queued on stream `s`.
+struct PhaseRange : Range {
+  PhaseRange(const char* n, cudaStream_t st) : Range(n), s(st) {}
+  ~PhaseRange() {
+    if (profile_enabled()) cudaStreamSynchronize(s);
+  }
+  cudaStream_t s;
 };
 
 // ---------------------------------------------------------------------------

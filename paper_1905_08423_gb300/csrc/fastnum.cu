@@ -157,7 +157,10 @@ int prepare_fast(ptap_plan* p) {
   PTAP_TRY(prepare_schedule(p));
   // optional: the interpreter runs if it fails; batch-only specialisation
   // leaves the compile to ptap_batch_create
-  if (p->cfg.jit && p->cfg.jit_scope == 0) jit_prepare(p);
+  if (p->cfg.jit && p->cfg.jit_scope == 0) {
+    PhaseRange r("ptap: specialise classes (NVRTC)", p->stream);
+    jit_prepare(p);
+  }
   return PTAP_OK;
 }
 

@@ -400,6 +400,7 @@ static int union_pattern(Tracker& mem, const E& ex, int32_t nrows, int32_t ncols
   // --- count pass (rows of at most 32 columns also keep them in a stash, when
   //     the 128 bytes a row fit: the fill pass then only copies those rows)
   PTAP_TRY(sc.get(&l1, std::max<int64_t>(nrows, 1)));
+  PhaseRange r_count("ptap: union count pass", s);
   int32_t* stash = nullptr;
   if (nrows > 0 && (int64_t)nrows * 128 <= ((int64_t)2 << 30) && mem.get_n(&stash, (int64_t)nrows * 32) != PTAP_OK)
     stash = nullptr;
@@ -450,6 +451,7 @@ static int union_pattern(Tracker& mem, const E& ex, int32_t nrows, int32_t ncols
   *nnz = total;
   PTAP_TRY(mem.get_n(ci, total));
   // --- fill pass
+  PhaseRange r_fill("ptap: union fill pass", s);
   if (nrows > 0) {
     k_union_warp<E, true><<<grid_w, threads, warp_smem, s>>>(ex, nrows, t.warp_log2, t.warp_limit,
                                                               tier, cnt, rp, *ci, nullptr, nullptr, nullptr);
@@ -936,10 +938,13 @@ static int symbolic_body(ptap_plan* p, const ptap_csr* A, const ptap_csr* P) {
     PTAP_TRY(sc.get(&tp, (int64_t)m + 1));
     PTAP_TRY(sc.get(&tj, p->nnz_p));
     CsrI Pi{P->nrows, P->ncols, P->row_ptr, P->col_idx};
-    PTAP_TRY(transpose_pattern(p->mem, Pi, tp, tj, nullptr, s));
+    {
+      PhaseRange r1("ptap: transpose of P's pattern", s);
+      PTAP_TRY(transpose_pattern(p->mem, Pi, tp, tj, nullptr, s));
+    }
     Expand3 ex{CsrI{m, P->nrows, tp, tj}, CsrI{A->nrows, A->ncols, A->row_ptr, A->col_idx}, Pi};
     int spilled = 0;
-    Range range("ptap: pattern of C");
+    PhaseRange range("ptap: pattern of C", s);
     PTAP_TRY(union_pattern(p->mem, ex, m, m, p->cfg, p->c_rp, &p->c_ci, &p->nnz_c, p->status,
                            &spilled, s));
     p->spill_rows = spilled;
@@ -960,7 +965,7 @@ static int symbolic_body(ptap_plan* p, const ptap_csr* A, const ptap_csr* P) {
   p->cfg.chunk_entries = user_ch ? std::min(user_value, try_fast ? ch_fast_max : ch_general_max)
                                  : (try_fast ? ch_fast : ch_general);
   {
-    Range range("ptap: chunk schedule");
+    PhaseRange range("ptap: chunk schedule", s);
     bool compact = false;
     if (try_fast && p->cfg.compact_chunks) {
       PTAP_TRY(build_schedule_compact(p, P, s, &compact));
@@ -969,7 +974,7 @@ static int symbolic_body(ptap_plan* p, const ptap_csr* A, const ptap_csr* P) {
     if (!compact) PTAP_TRY(build_schedule(p, P, s));
   }
   if (try_fast) {
-    Range range("ptap: structure classes");
+    PhaseRange range("ptap: structure classes", s);
     PTAP_TRY(build_classes(p, A, P, s));
     const int general_ch = user_ch ? std::min(user_value, ch_general_max) : ch_general;
     if (!p->fast && (p->cfg.chunk_entries != general_ch || p->compact)) {
@@ -981,7 +986,7 @@ static int symbolic_body(ptap_plan* p, const ptap_csr* A, const ptap_csr* P) {
   if (!p->fast) p->cfg.block_threads = std::min(p->cfg.block_threads, 256);
   PTAP_TRY(build_index_cache(p, A, P, s));
   {
-    Range range("ptap: prepare numeric (code generation)");
+    PhaseRange range("ptap: prepare numeric (code generation)", s);
     PTAP_TRY(prepare_numeric(p));
   }
   PTAP_CUDA(cudaStreamSynchronize(s));
