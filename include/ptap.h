@@ -294,6 +294,52 @@ int ptap_gather(const void* src, const int32_t* src_idx, int64_t n, int32_t dtyp
 int ptap_scatter_add(const void* src, const int32_t* src_idx, const int32_t* dst_idx, int64_t n,
                      int32_t dtype, void* dst, void* stream);
 
+/* ---- levels of an algebraic multigrid hierarchy ---------------------------
+ * The paper's application forms a twelve-level hierarchy with eleven triple
+ * products (Section 4.2.2, Tables 5-6), taking its coarsening from a cited
+ * work.  These calls build one reading of it on the device -- smoothed
+ * aggregation -- so that C = P^T A P of every level runs through this
+ * library: aggregate the fine rows, form P = (I - omega D^-1 A) T from the
+ * tentative prolongator T(i, agg(i)) = 1, then ptap_symbolic / ptap_numeric.
+ * A must be square, hold its diagonal and be symmetric in magnitude (the
+ * strength of an edge is |A(i,j)| read from row i).
+ *
+ * ptap_aggregate: repeated pairwise matching.  A round: every unmatched node
+ * picks the unmatched neighbour node with the largest key (strength, hash of
+ * the node pair), where the strength between two nodes is the largest
+ * |A(i,j)| over their members; mutual picks are matched.  Rounds repeat until
+ * none matches or `rounds` is reached; unmatched nodes stay alone.  Each of
+ * `passes` (0..8) passes matches the previous pass's nodes, so aggregates
+ * hold at most 2^passes rows.  Writes agg[i] (device, A.nrows entries,
+ * caller-owned) in 0..*n_agg-1 and *n_agg (host).  Deterministic.
+ * Synchronises `stream`; scratch comes from `alloc` (NULL: cudaMallocAsync)
+ * and is freed before return.  Errors: PTAP_ERR_INVALID, PTAP_ERR_OOM,
+ * PTAP_ERR_CUDA. */
+int ptap_aggregate(const ptap_csr* A, int32_t passes, int32_t rounds, int32_t* agg, int32_t* n_agg,
+                   const ptap_allocator* alloc, void* stream);
+
+/* The smoothed prolongator of an aggregation: an opaque, library-owned
+ * object holding the pattern of P = pattern(A T) (sorted columns), n x n_agg.
+ * ptap_prolongator_symbolic reads A's pattern and agg (copied); synchronises
+ * `stream`.  ptap_prolongator_pattern returns its sizes and device pointers
+ * (valid until destroy).  ptap_prolongator_numeric writes the nnz(P) values
+ * P(i,a) = [agg(i) = a] - omega / A(i,i) * sum_{j in A(i,:), agg(j) = a}
+ * A(i,j) into P_val (caller-owned device buffer of A's dtype); A must have
+ * the pattern given at symbolic time (PTAP_ERR_PATTERN); asynchronous,
+ * allocates nothing, and may be repeated whenever A's values change.
+ * ptap_prolongator_check reads and clears its device status word
+ * (PTAP_ERR_INVALID for a row without a diagonal entry).  Destroy frees it
+ * (NULL is a no-op). */
+typedef struct ptap_prolongator ptap_prolongator;
+int ptap_prolongator_symbolic(const ptap_csr* A, const int32_t* agg, int32_t n_agg,
+                              const ptap_allocator* alloc, void* stream, ptap_prolongator** out);
+int ptap_prolongator_pattern(const ptap_prolongator* P, int32_t* nrows, int32_t* ncols, int64_t* nnz,
+                             const int32_t** row_ptr, const int32_t** col_idx);
+int ptap_prolongator_numeric(ptap_prolongator* P, const ptap_csr* A, double omega, void* P_val,
+                             void* stream);
+int ptap_prolongator_check(ptap_prolongator* P, void* stream);
+void ptap_prolongator_destroy(ptap_prolongator* P);
+
 /* ---- batched numeric products that allocate nothing ---------------------
  * The paper has no counterpart to this entry point.  It serves callers that
  * cannot allocate device memory when the products run: solvers that reserve

@@ -83,7 +83,9 @@ SYMBOLS = ["ptap_symbolic", "ptap_plan_pattern", "ptap_numeric", "ptap_backward"
            "ptap_two_step_symbolic", "ptap_batch_create", "ptap_batch_numeric",
            "ptap_batch_destroy", "ptap_plan_stats", "ptap_plan_check", "ptap_plan_destroy",
            "ptap_error_string", "ptap_version", "ptap_gather", "ptap_scatter_add",
-           "ptap_numeric_host", "ptap_batch_numeric_noalloc"]
+           "ptap_numeric_host", "ptap_batch_numeric_noalloc", "ptap_aggregate",
+           "ptap_prolongator_symbolic", "ptap_prolongator_pattern", "ptap_prolongator_numeric",
+           "ptap_prolongator_check", "ptap_prolongator_destroy"]
 
 
 def lib_path() -> str:
@@ -478,3 +480,80 @@ def scatter_add(dst: torch.Tensor, dst_idx: torch.Tensor, src: torch.Tensor,
                                    dst_idx.data_ptr(), n, _vcode(dst), dst.data_ptr(), _stream(stream)),
            "ptap_scatter_add")
     return dst
+
+
+# ---------------------------------------------------------------------------
+# levels of an algebraic multigrid hierarchy (aggregation, smoothed prolongator)
+# ---------------------------------------------------------------------------
+def _amg_sigs(L):
+    if getattr(L, "_amg_sigs", False):
+        return
+    L.ptap_aggregate.argtypes = [_c.POINTER(_Csr), _c.c_int32, _c.c_int32, _VP, _c.POINTER(_c.c_int32),
+                                 _c.POINTER(_Allocator), _VP]
+    L.ptap_prolongator_symbolic.argtypes = [_c.POINTER(_Csr), _VP, _c.c_int32, _c.POINTER(_Allocator), _VP, _PP]
+    L.ptap_prolongator_pattern.argtypes = [_VP, _c.POINTER(_c.c_int32), _c.POINTER(_c.c_int32),
+                                           _c.POINTER(_c.c_int64), _PP, _PP]
+    L.ptap_prolongator_numeric.argtypes = [_VP, _c.POINTER(_Csr), _c.c_double, _VP, _VP]
+    L.ptap_prolongator_check.argtypes = [_VP, _VP]
+    L.ptap_prolongator_destroy.argtypes = [_VP]
+    L.ptap_prolongator_destroy.restype = None
+    L._amg_sigs = True
+
+
+def aggregate(A: Csr, passes: int = 2, rounds: int = 16, stream=None):
+    """ptap_aggregate: (agg, n_agg) -- the aggregate of every row of A (int32 device tensor)."""
+    L = _lib()
+    _amg_sigs(L)
+    agg = torch.empty(max(A.nrows, 1), dtype=torch.int32, device=A.row_ptr.device)
+    n = _c.c_int32()
+    _check(L.ptap_aggregate(_c.byref(A.c()), passes, rounds, agg.data_ptr(), _c.byref(n),
+                            _c.byref(_TORCH_ALLOCATOR), _stream(stream)), "ptap_aggregate")
+    return agg[:A.nrows], n.value
+
+
+class Prolongator:
+    """ptap_prolongator_*: the pattern of P = (I - omega D^-1 A) T, and its values on demand."""
+
+    def __init__(self, A: Csr, agg: torch.Tensor, n_agg: int, stream=None):
+        L = _lib()
+        _amg_sigs(L)
+        assert agg.dtype == torch.int32 and agg.is_cuda and agg.numel() == A.nrows
+        h = _c.c_void_p()
+        _check(L.ptap_prolongator_symbolic(_c.byref(A.c()), agg.contiguous().data_ptr(), n_agg,
+                                           _c.byref(_TORCH_ALLOCATOR), _stream(stream), _c.byref(h)),
+               "ptap_prolongator_symbolic")
+        self._h = h
+        self.n, self.m = A.nrows, n_agg
+        nr, nc, nnz, rp, ci = _c.c_int32(), _c.c_int32(), _c.c_int64(), _c.c_void_p(), _c.c_void_p()
+        _check(L.ptap_prolongator_pattern(h, _c.byref(nr), _c.byref(nc), _c.byref(nnz), _c.byref(rp),
+                                          _c.byref(ci)), "ptap_prolongator_pattern")
+        self.nnz = nnz.value
+        dev = A.row_ptr.device
+        self.row_ptr = torch.as_tensor(_DevArray(rp.value, nr.value + 1, "<i4"), device=dev).clone()
+        self.col_idx = (torch.as_tensor(_DevArray(ci.value, self.nnz, "<i4"), device=dev).clone()
+                        if self.nnz > 0 else torch.zeros(0, dtype=torch.int32, device=dev))
+
+    def numeric(self, A: Csr, omega: float = 2.0 / 3.0, out: torch.Tensor | None = None, stream=None):
+        if out is None:
+            out = torch.empty(self.nnz, dtype=A.val.dtype, device=A.val.device)
+        assert out.is_contiguous() and out.numel() == self.nnz and out.dtype == A.val.dtype
+        _check(_lib().ptap_prolongator_numeric(self._h, _c.byref(A.c()), float(omega), out.data_ptr(),
+                                               _stream(stream)), "ptap_prolongator_numeric")
+        return out
+
+    def csr(self, val: torch.Tensor) -> Csr:
+        return Csr(self.n, self.m, self.row_ptr, self.col_idx, val)
+
+    def check(self, stream=None):
+        _check(_lib().ptap_prolongator_check(self._h, _stream(stream)), "prolongator status")
+
+    def destroy(self):
+        if self._h:
+            _lib().ptap_prolongator_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
