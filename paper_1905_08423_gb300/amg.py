@@ -5,7 +5,9 @@ products C = P^T A P (Section 4.2.2, Tables 5-6), one per level, in the
 setup phase of its preconditioner, and repeats that setup as the operator's
 values change.  ``Hierarchy`` does the same on one GPU: per level it
 aggregates the rows (ptap_aggregate), forms the smoothed prolongator P =
-(I - omega D^-1 A) T (ptap_prolongator_*), and forms the next operator with
+(I - omega D_F^-1 A_F) T, A_F the operator filtered by strength theta
+(ptap_prolongator_*; filtering keeps the coarse operators sparse, as the rows
+of Tables 5-6 are), and forms the next operator with
 ptap_symbolic / ptap_numeric; the coarse operator is the next level's A.
 
 ``renumeric`` re-runs only the numeric phases -- every level's P values and
@@ -38,8 +40,8 @@ class Hierarchy:
     at most ``coarse_rows`` rows or ``max_levels`` operators."""
 
     def __init__(self, A: ptap.Csr, max_levels: int = 12, coarse_rows: int = 400, passes: int = 2,
-                 rounds: int = 16, omega: float = 2.0 / 3.0, config=None):
-        self.omega = omega
+                 rounds: int = 16, omega: float = 2.0 / 3.0, theta: float = 0.5, config=None):
+        self.omega, self.theta, self.passes, self.rounds = omega, theta, passes, rounds
         self.levels: list[Level] = []
         self.coarse: ptap.Csr = A
         cur = A
@@ -47,7 +49,7 @@ class Hierarchy:
             agg, n_agg = ptap.aggregate(cur, passes, rounds)
             if n_agg >= cur.nrows:       # no coarsening possible
                 break
-            prol = ptap.Prolongator(cur, agg, n_agg)
+            prol = ptap.Prolongator(cur, agg, n_agg, theta)
             P = prol.csr(prol.numeric(cur, omega))
             plan = ptap.symbolic(cur, P, config)
             C = ptap.numeric(plan, cur, P)

@@ -147,16 +147,53 @@ __global__ void k_one_per_row(int32_t n, int32_t* __restrict__ rp) {
   for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i <= n; i += gridDim.x * blockDim.x) rp[i] = i;
 }
 
-// Values of P = (I - omega D^-1 A) T on its sorted pattern: one thread a row.
+// Strength of the entries of A: mask[e] = 1 for an off-diagonal entry with
+// |A(i,j)| >= theta * max_{k != i} |A(i,k)| (theta = 0: every off-diagonal
+// entry), 0 for the diagonal and for weak entries.  Settled once, at
+// symbolic time, so the prolongator's pattern does not move with the values.
 template <typename V>
-__global__ void k_prolong_values(CsrV<V> A, const int32_t* __restrict__ agg, const int32_t* __restrict__ prp,
-                                 const int32_t* __restrict__ pci, double omega, V* __restrict__ pval,
-                                 int32_t* status) {
+__global__ void k_strong(CsrV<V> A, double theta, uint8_t* __restrict__ mask, int32_t* __restrict__ cnt) {
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < A.nrows; i += gridDim.x * blockDim.x) {
+    double mx = 0.0;
+    for (int32_t e = A.rp[i]; e < A.rp[i + 1]; ++e)
+      if (A.ci[e] != i) mx = fmax(mx, fabs((double)A.val[e]));
+    const double thr = theta * mx;
+    int32_t c = 1;  // the diagonal position of the filtered row
+    for (int32_t e = A.rp[i]; e < A.rp[i + 1]; ++e) {
+      const bool st = A.ci[e] != i && fabs((double)A.val[e]) >= thr;
+      mask[e] = st ? 1 : 0;
+      c += st ? 1 : 0;
+    }
+    cnt[i] = c;
+  }
+}
+
+// Pattern of the filtered operator: the diagonal and the strong entries.
+__global__ void k_filtered_fill(CsrI A, const uint8_t* __restrict__ mask, const int32_t* __restrict__ frp,
+                                int32_t* __restrict__ fci) {
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < A.nrows; i += gridDim.x * blockDim.x) {
+    int32_t o = frp[i];
+    fci[o++] = i;
+    for (int32_t e = A.rp[i]; e < A.rp[i + 1]; ++e)
+      if (mask[e]) fci[o++] = A.ci[e];
+  }
+}
+
+// Values of P = (I - omega D_F^-1 A_F) T on its sorted pattern, one thread a
+// row: A_F keeps the diagonal and the strong entries, and its diagonal D_F
+// also collects the weak entries (lumping), so A_F 1 = A 1.
+template <typename V>
+__global__ void k_prolong_values(CsrV<V> A, const uint8_t* __restrict__ mask, const int32_t* __restrict__ agg,
+                                 const int32_t* __restrict__ prp, const int32_t* __restrict__ pci, double omega,
+                                 V* __restrict__ pval, int32_t* status) {
   for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < A.nrows; i += gridDim.x * blockDim.x) {
     const int32_t p0 = prp[i], p1 = prp[i + 1];
     V d = V(0);
-    for (int32_t e = A.rp[i]; e < A.rp[i + 1]; ++e)
-      if (A.ci[e] == i) d = A.val[e];
+    bool has_diag = false;
+    for (int32_t e = A.rp[i]; e < A.rp[i + 1]; ++e) {
+      if (A.ci[e] == i) has_diag = true;
+      if (!mask[e]) d += A.val[e];
+    }
     for (int32_t q = p0; q < p1; ++q) pval[q] = V(0);
     auto pos = [&](int32_t a) {
       int32_t lo = p0, hi = p1;
@@ -168,13 +205,14 @@ __global__ void k_prolong_values(CsrV<V> A, const int32_t* __restrict__ agg, con
       return (lo < p1 && pci[lo] == a) ? lo : -1;
     };
     const int32_t own = pos(agg[i]);
-    if (own < 0 || d == V(0)) {
-      atomicExch(status, PTAP_ERR_INVALID);  // no diagonal entry, or the pattern is not A T's
+    if (own < 0 || !has_diag || d == V(0)) {
+      atomicExch(status, PTAP_ERR_INVALID);  // no diagonal entry, or the pattern is not this P's
       continue;
     }
-    pval[own] = V(1);
+    pval[own] = V(1) - (V)omega;   // the filtered diagonal's own term: 1 - omega d / d
     const V f = (V)(omega) / d;
     for (int32_t e = A.rp[i]; e < A.rp[i + 1]; ++e) {
+      if (!mask[e]) continue;
       const int32_t q = pos(agg[A.ci[e]]);
       if (q < 0) {
         atomicExch(status, PTAP_ERR_PATTERN);
@@ -196,6 +234,7 @@ struct ptap_prolongator {
   int32_t n = 0, m = 0;
   int64_t nnz_a = 0, nnz = 0;
   int32_t* agg = nullptr;  // copy of the aggregate of every fine row
+  uint8_t* mask = nullptr; // strong entries of A (settled at symbolic time)
   int32_t* rp = nullptr;
   int32_t* ci = nullptr;
   int32_t* status = nullptr;
@@ -289,14 +328,15 @@ extern "C" int ptap_aggregate(const ptap_csr* A, int32_t passes, int32_t rounds,
   return rc;
 }
 
-extern "C" int ptap_prolongator_symbolic(const ptap_csr* A, const int32_t* agg, int32_t n_agg,
+extern "C" int ptap_prolongator_symbolic(const ptap_csr* A, const int32_t* agg, int32_t n_agg, double theta,
                                          const ptap_allocator* alloc, void* stream, ptap_prolongator** out) {
   using namespace ptap;
   Range range("ptap_prolongator_symbolic");
   if (!A || !agg || !out || n_agg < 0) return PTAP_ERR_INVALID;
   *out = nullptr;
-  PTAP_TRY(check_csr_host(A, false));
-  if (A->nrows != A->ncols || (A->nrows > 0 && n_agg < 1)) return PTAP_ERR_INVALID;
+  PTAP_TRY(check_csr_host(A, true));  // the strength of connection reads A's values
+  if (A->nrows != A->ncols || (A->nrows > 0 && n_agg < 1) || !(theta >= 0.0 && theta <= 1.0))
+    return PTAP_ERR_INVALID;
   cudaStream_t s = (cudaStream_t)stream;
   ptap_prolongator* p = new (std::nothrow) ptap_prolongator();
   if (!p) return PTAP_ERR_OOM;
@@ -312,13 +352,29 @@ extern "C" int ptap_prolongator_symbolic(const ptap_csr* A, const int32_t* agg, 
     PTAP_TRY(p->mem.get_n(&p->rp, (int64_t)p->n + 1));
     if (p->n > 0)
       PTAP_CUDA(cudaMemcpyAsync(p->agg, agg, (size_t)p->n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
-    // pattern of A T, T the tentative prolongator (one entry a row)
+    // strong entries, the filtered operator's pattern, then the pattern of
+    // A_F T (T the tentative prolongator: one entry a row)
     Scratch sc(&p->mem);
-    int32_t* trp = nullptr;
+    int32_t *trp = nullptr, *fcnt = nullptr, *frp = nullptr, *fci = nullptr;
+    PTAP_TRY(p->mem.get_n(&p->mask, std::max<int64_t>(p->nnz_a, 1)));
     PTAP_TRY(sc.get(&trp, (int64_t)p->n + 1));
+    PTAP_TRY(sc.get(&fcnt, (int64_t)p->n + 1));
+    PTAP_TRY(sc.get(&frp, (int64_t)p->n + 1));
     k_one_per_row<<<grid_of(p->n + 1), 256, 0, s>>>(p->n, trp);
+    if (A->dtype == PTAP_F64)
+      k_strong<double><<<grid_of(p->n), 256, 0, s>>>(
+          CsrV<double>{A->nrows, A->ncols, A->row_ptr, A->col_idx, (const double*)A->val}, theta, p->mask, fcnt);
+    else
+      k_strong<float><<<grid_of(p->n), 256, 0, s>>>(
+          CsrV<float>{A->nrows, A->ncols, A->row_ptr, A->col_idx, (const float*)A->val}, theta, p->mask, fcnt);
     PTAP_LAUNCHED();
-    CsrI Ai{A->nrows, A->ncols, A->row_ptr, A->col_idx};
+    int64_t fnnz = 0;
+    PTAP_TRY(exclusive_scan(p->mem, fcnt, frp, p->n, &fnnz, s));
+    PTAP_TRY(sc.get(&fci, std::max<int64_t>(fnnz, 1)));
+    k_filtered_fill<<<grid_of(p->n), 256, 0, s>>>(CsrI{A->nrows, A->ncols, A->row_ptr, A->col_idx}, p->mask,
+                                                   frp, fci);
+    PTAP_LAUNCHED();
+    CsrI Ai{A->nrows, A->ncols, frp, fci};
     CsrI Ti{p->n, n_agg, trp, p->agg};
     Config cfg;
     int spilled = 0;
@@ -362,12 +418,12 @@ extern "C" int ptap_prolongator_numeric(ptap_prolongator* p, const ptap_csr* A, 
   cudaStream_t s = (cudaStream_t)stream;
   if (A->dtype == PTAP_F64)
     k_prolong_values<double><<<grid_of(p->n), 256, 0, s>>>(
-        CsrV<double>{A->nrows, A->ncols, A->row_ptr, A->col_idx, (const double*)A->val}, p->agg, p->rp, p->ci,
-        omega, (double*)P_val, p->status);
+        CsrV<double>{A->nrows, A->ncols, A->row_ptr, A->col_idx, (const double*)A->val}, p->mask, p->agg, p->rp,
+        p->ci, omega, (double*)P_val, p->status);
   else
     k_prolong_values<float><<<grid_of(p->n), 256, 0, s>>>(
-        CsrV<float>{A->nrows, A->ncols, A->row_ptr, A->col_idx, (const float*)A->val}, p->agg, p->rp, p->ci,
-        omega, (float*)P_val, p->status);
+        CsrV<float>{A->nrows, A->ncols, A->row_ptr, A->col_idx, (const float*)A->val}, p->mask, p->agg, p->rp,
+        p->ci, omega, (float*)P_val, p->status);
   PTAP_LAUNCHED();
   return PTAP_OK;
 }

@@ -490,7 +490,8 @@ def _amg_sigs(L):
         return
     L.ptap_aggregate.argtypes = [_c.POINTER(_Csr), _c.c_int32, _c.c_int32, _VP, _c.POINTER(_c.c_int32),
                                  _c.POINTER(_Allocator), _VP]
-    L.ptap_prolongator_symbolic.argtypes = [_c.POINTER(_Csr), _VP, _c.c_int32, _c.POINTER(_Allocator), _VP, _PP]
+    L.ptap_prolongator_symbolic.argtypes = [_c.POINTER(_Csr), _VP, _c.c_int32, _c.c_double,
+                                            _c.POINTER(_Allocator), _VP, _PP]
     L.ptap_prolongator_pattern.argtypes = [_VP, _c.POINTER(_c.c_int32), _c.POINTER(_c.c_int32),
                                            _c.POINTER(_c.c_int64), _PP, _PP]
     L.ptap_prolongator_numeric.argtypes = [_VP, _c.POINTER(_Csr), _c.c_double, _VP, _VP]
@@ -512,14 +513,15 @@ def aggregate(A: Csr, passes: int = 2, rounds: int = 16, stream=None):
 
 
 class Prolongator:
-    """ptap_prolongator_*: the pattern of P = (I - omega D^-1 A) T, and its values on demand."""
+    """ptap_prolongator_*: the pattern of P = (I - omega D_F^-1 A_F) T (A_F: A filtered by
+    strength theta, dropped entries lumped into its diagonal), and its values on demand."""
 
-    def __init__(self, A: Csr, agg: torch.Tensor, n_agg: int, stream=None):
+    def __init__(self, A: Csr, agg: torch.Tensor, n_agg: int, theta: float = 0.0, stream=None):
         L = _lib()
         _amg_sigs(L)
         assert agg.dtype == torch.int32 and agg.is_cuda and agg.numel() == A.nrows
         h = _c.c_void_p()
-        _check(L.ptap_prolongator_symbolic(_c.byref(A.c()), agg.contiguous().data_ptr(), n_agg,
+        _check(L.ptap_prolongator_symbolic(_c.byref(A.c()), agg.contiguous().data_ptr(), n_agg, float(theta),
                                            _c.byref(_TORCH_ALLOCATOR), _stream(stream), _c.byref(h)),
                "ptap_prolongator_symbolic")
         self._h = h

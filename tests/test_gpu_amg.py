@@ -29,9 +29,10 @@ def _host(M: ptap.Csr) -> pb.CSR:
                   M.val.detach().cpu().numpy().astype(np.float64))
 
 
+@pytest.mark.parametrize("theta", [0.0, 0.25])
 @pytest.mark.parametrize("passes", [1, 2, 3])
 @pytest.mark.parametrize("kind", ["algebraic", "poisson2d", "model"])
-def test_aggregate_and_prolongator(kind, passes):
+def test_aggregate_and_prolongator(kind, passes, theta):
     A = {"algebraic": lambda: pb.algebraic_problem(12, seed=5)[0],
          "poisson2d": lambda: pb.poisson2d_problem(40)[0],
          "model": lambda: pb.model_problem(13)[0]}[kind]()
@@ -40,15 +41,26 @@ def test_aggregate_and_prolongator(kind, passes):
     want, n_want = oamg.aggregate(A, passes=passes, rounds=16)
     assert n_agg == n_want
     np.testing.assert_array_equal(agg.cpu().numpy(), want)
-    prol = ptap.Prolongator(dA, agg, n_agg)
+    prol = ptap.Prolongator(dA, agg, n_agg, theta)
     P = prol.numeric(dA, 2.0 / 3.0)
     torch.cuda.synchronize()
     prol.check()
-    rp, ci, v = oamg.prolongator(A, want, n_want, 2.0 / 3.0)
+    rp, ci, v = oamg.prolongator(A, want, n_want, 2.0 / 3.0, theta)
     np.testing.assert_array_equal(prol.row_ptr.cpu().numpy(), rp)
     np.testing.assert_array_equal(prol.col_idx.cpu().numpy(), ci)
     np.testing.assert_allclose(P.cpu().numpy(), v, rtol=1e-13, atol=1e-13)
     prol.destroy()
+
+
+def _tau(A, P, dtype):
+    """Value tolerance of one level.  FP64: tau = 1e-12.  FP32: the product accumulates
+    each entry in FP32 over at most k = (longest column of P) + (longest row of A) + 2
+    roundings, so |error| <= k * 2^-24 * B; tau = max(1e-5, k * 2^-24)."""
+    if dtype == torch.float64:
+        return TAU[dtype]
+    kcol = int(np.bincount(P.col_idx, minlength=P.ncols).max()) if P.nnz else 0
+    krow = int(np.diff(A.row_ptr).max()) if A.nrows else 0
+    return max(TAU[dtype], (kcol + krow + 2) * 2.0 ** -24)
 
 
 def _check_levels(h: amg.Hierarchy, dtype):
@@ -56,7 +68,7 @@ def _check_levels(h: amg.Hierarchy, dtype):
     h.check()
     for k, lv in enumerate(h.levels):
         A, P = _host(lv.A), _host(lv.P)
-        rp, ci, v = oamg.prolongator(A, lv.agg.cpu().numpy(), lv.P.ncols, h.omega)
+        rp, ci, v = oamg.prolongator(A, lv.agg.cpu().numpy(), lv.P.ncols, h.omega, h.theta)
         np.testing.assert_array_equal(lv.P.row_ptr.cpu().numpy(), rp)
         np.testing.assert_array_equal(lv.P.col_idx.cpu().numpy(), ci)
         tol = 1e-13 if dtype == torch.float64 else 1e-5
@@ -66,7 +78,8 @@ def _check_levels(h: amg.Hierarchy, dtype):
         np.testing.assert_array_equal(crp.cpu().numpy(), ref.row_ptr)
         np.testing.assert_array_equal(cci.cpu().numpy(), ref.col_idx)
         err = np.abs(lv.C.cpu().numpy().astype(np.float64) - ref.val)
-        assert np.all(np.where(bnd.val > 0, err <= TAU[dtype] * bnd.val, err == 0)), k
+        tau = _tau(A, P, dtype)
+        assert np.all(np.where(bnd.val > 0, err <= tau * bnd.val, err == 0)), (k, tau)
 
 
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
