@@ -308,7 +308,10 @@ int ptap_scatter_add(const void* src, const int32_t* src_idx, const int32_t* dst
  * picks the unmatched neighbour node with the largest key (strength, hash of
  * the node pair), where the strength between two nodes is the largest
  * |A(i,j)| over their members; mutual picks are matched.  Rounds repeat until
- * none matches or `rounds` is reached; unmatched nodes stay alone.  Each of
+ * none matches or `rounds` is reached; then up to `rounds` more rounds key
+ * the edges by the hash alone (random priorities, which converge fast where
+ * long chains of decreasing strength slow the first phase); unmatched nodes
+ * stay alone.  Each of
  * `passes` (0..8) passes matches the previous pass's nodes, so aggregates
  * hold at most 2^passes rows.  Writes agg[i] (device, A.nrows entries,
  * caller-owned) in 0..*n_agg-1 and *n_agg (host).  Deterministic.

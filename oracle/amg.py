@@ -14,7 +14,7 @@ on both sides is smoothed aggregation:
   edge_hash(a, b), then the smaller node on a full tie), the strength of two
   nodes being the largest |A(i,j)| between their members; nodes that picked
   each other form a pair.  Rounds repeat until none pairs or ``rounds`` is
-  reached.  A pass turns pairs and lone nodes into the next pass's nodes,
+  reached; then up to ``rounds`` more rounds key the edges by the hash alone.  A pass turns pairs and lone nodes into the next pass's nodes,
   numbered by their smaller old node; ``passes`` passes give aggregates of at
   most 2^passes rows.
 * ``prolongator`` -- P = (I - omega D_F^-1 A_F) T with T(i, agg(i)) = 1 and
@@ -69,22 +69,24 @@ def aggregate(A, passes: int = 2, rounds: int = 16):
             break
         edges = [_node_edges(A, node_of, members, a) for a in range(nn)]
         partner = [-1] * nn
-        for _ in range(rounds):
-            pick = [-1] * nn
-            for a in range(nn):
-                if partner[a] >= 0:
-                    continue
-                cand = [(w, edge_hash(a, b), -b) for b, w in edges[a].items() if partner[b] < 0]
-                if cand:
-                    pick[a] = -max(cand)[2]
-            matched = 0
-            for a in range(nn):
-                b = pick[a]
-                if b >= 0 and pick[b] == a:
-                    partner[a] = b
-                    matched += a < b
-            if matched == 0:
-                break
+        for phase in ("strength", "hash"):
+            for _ in range(rounds):
+                pick = [-1] * nn
+                for a in range(nn):
+                    if partner[a] >= 0:
+                        continue
+                    cand = [(w if phase == "strength" else 0.0, edge_hash(a, b), -b)
+                            for b, w in edges[a].items() if partner[b] < 0]
+                    if cand:
+                        pick[a] = -max(cand)[2]
+                matched = 0
+                for a in range(nn):
+                    b = pick[a]
+                    if b >= 0 and pick[b] == a:
+                        partner[a] = b
+                        matched += a < b
+                if matched == 0:
+                    break
         leaders = [a for a in range(nn) if partner[a] < 0 or a < partner[a]]
         new_id = {a: k for k, a in enumerate(leaders)}
         new_members = []
@@ -119,21 +121,23 @@ def greedy_matching(A):
     return partner
 
 
-def prolongator(A, agg, n_agg: int, omega: float = 2.0 / 3.0, theta: float = 0.0):
+def prolongator(A, agg, n_agg: int, omega: float = 2.0 / 3.0, theta: float = 0.0, S=None):
     """P = (I - omega D_F^-1 A_F) T as (row_ptr, col_idx, val) on the pattern of A_F T.
 
     A_F keeps the diagonal and the off-diagonal entries with |A(i,j)| >=
     theta * max_{k != i} |A(i,k)|; the dropped entries are added to its
     diagonal D_F (so A_F 1 = A 1).  Structural: entries are kept when their
-    value is zero.
+    value is zero.  S (A's pattern, other values) decides the strong entries
+    instead of A when given: a hierarchy settles them once, at setup.
     """
+    S = A if S is None else S
     n = A.nrows
     rp_out, ci_out, val_out = [0], [], []
     for i in range(n):
         lo, hi = int(A.row_ptr[i]), int(A.row_ptr[i + 1])
         off = [e for e in range(lo, hi) if int(A.col_idx[e]) != i]
-        mx = max((abs(float(A.val[e])) for e in off), default=0.0)
-        strong = [e for e in off if abs(float(A.val[e])) >= theta * mx]
+        mx = max((abs(float(S.val[e])) for e in off), default=0.0)
+        strong = [e for e in off if abs(float(S.val[e])) >= theta * mx]
         sset = set(strong)
         d = 0.0
         for e in range(lo, hi):

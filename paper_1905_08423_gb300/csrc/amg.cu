@@ -11,7 +11,9 @@
 //    ends, so the globally strongest edge is always mutual and every round
 //    makes progress (locally dominant edges).  Strength between two nodes
 //    is the largest |A(i,j)| over their members i, j (a maximum, exact in
-//    any order).  Rounds repeat until none matches or `rounds` is reached;
+//    any order).  Rounds repeat until none matches or `rounds` is reached,
+//    then up to `rounds` more rounds key the edges by the hash alone (random
+//    priorities, which mop up what long chains of decreasing strength left);
 //    nodes left unmatched stay alone.  Pass k matches the nodes of pass k-1,
 //    so `passes` passes give aggregates of at most 2^passes fine rows.
 //  * Tentative prolongator T(i, agg(i)) = 1 and the smoothed prolongator
@@ -50,10 +52,13 @@ __device__ inline bool stronger(double w1, uint32_t h1, double w2, uint32_t h2) 
 // One round of picks.  Node a (members mem_ptr[a] .. mem_ptr[a+1] of the
 // fine rows, listed in members) picks the unmatched node b != a with the
 // strongest edge; pick[a] = b, or -1 if it is matched or has no candidate.
+// With use_strength false the key is the hash alone (random priorities: the
+// rounds that mop up nodes that long chains of decreasing strength left
+// unmatched converge fast).
 template <typename V>
 __global__ void k_pick(CsrV<V> A, const int32_t* __restrict__ node_of, const int32_t* __restrict__ mem_ptr,
                        const int32_t* __restrict__ members, int32_t nnodes, const int32_t* __restrict__ partner,
-                       int32_t* __restrict__ pick) {
+                       int32_t* __restrict__ pick, bool use_strength) {
   for (int32_t a = blockIdx.x * blockDim.x + threadIdx.x; a < nnodes; a += gridDim.x * blockDim.x) {
     int32_t best = -1;
     double bw = -1.0;
@@ -64,7 +69,7 @@ __global__ void k_pick(CsrV<V> A, const int32_t* __restrict__ node_of, const int
         for (int32_t e = A.rp[i]; e < A.rp[i + 1]; ++e) {
           const int32_t b = node_of[A.ci[e]];
           if (b == a || partner[b] >= 0) continue;
-          const double w = fabs((double)A.val[e]);
+          const double w = use_strength ? fabs((double)A.val[e]) : 0.0;
           const uint32_t h = edge_hash(a, b);
           if (stronger(w, h, bw, bh) || (w == bw && h == bh && b < best)) {
             best = b;
@@ -272,15 +277,21 @@ int aggregate_t(const ptap_csr* Ain, int32_t passes, int32_t rounds, int32_t* ag
   int32_t nnodes = n;
   for (int32_t pass = 0; pass < passes && nnodes > 1; ++pass) {
     PTAP_CUDA(cudaMemsetAsync(partner, 0xff, (size_t)nnodes * sizeof(int32_t), s));
-    for (int32_t r = 0; r < rounds; ++r) {
+    // `rounds` rounds keyed by strength, then up to `rounds` keyed by the hash
+    // alone; a round that matches nothing ends its phase
+    for (int32_t r = 0; r < 2 * rounds; ++r) {
+      const bool strength = r < rounds;
       PTAP_CUDA(cudaMemsetAsync(counter, 0, sizeof(int32_t), s));
-      k_pick<V><<<grid_of(nnodes), 256, 0, s>>>(A, node_of, mem_ptr, members, nnodes, partner, pick);
+      k_pick<V><<<grid_of(nnodes), 256, 0, s>>>(A, node_of, mem_ptr, members, nnodes, partner, pick, strength);
       k_match<<<grid_of(nnodes), 256, 0, s>>>(pick, nnodes, partner, counter);
       PTAP_LAUNCHED();
       int32_t matched = 0;
       PTAP_CUDA(cudaMemcpyAsync(&matched, counter, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
       PTAP_CUDA(cudaStreamSynchronize(s));
-      if (matched == 0) break;
+      if (matched == 0) {
+        if (!strength) break;
+        r = rounds - 1;  // on to the hash-keyed rounds
+      }
     }
     // new nodes: leaders in order of their old id
     k_leaders<<<grid_of(nnodes), 256, 0, s>>>(partner, nnodes, lead);

@@ -63,12 +63,14 @@ def _tau(A, P, dtype):
     return max(TAU[dtype], (kcol + krow + 2) * 2.0 ** -24)
 
 
-def _check_levels(h: amg.Hierarchy, dtype):
+def _check_levels(h: amg.Hierarchy, dtype, strength):
+    """Every level against the oracle; ``strength`` holds each level's operator as it was
+    at setup, whose values decided the strong entries (fixed with the pattern)."""
     torch.cuda.synchronize()
     h.check()
     for k, lv in enumerate(h.levels):
         A, P = _host(lv.A), _host(lv.P)
-        rp, ci, v = oamg.prolongator(A, lv.agg.cpu().numpy(), lv.P.ncols, h.omega, h.theta)
+        rp, ci, v = oamg.prolongator(A, lv.agg.cpu().numpy(), lv.P.ncols, h.omega, h.theta, S=strength[k])
         np.testing.assert_array_equal(lv.P.row_ptr.cpu().numpy(), rp)
         np.testing.assert_array_equal(lv.P.col_idx.cpu().numpy(), ci)
         tol = 1e-13 if dtype == torch.float64 else 1e-5
@@ -93,7 +95,8 @@ def test_hierarchy_levels(dtype):
             want, n_want = oamg.aggregate(_host(lv.A), passes=2, rounds=16)
             assert lv.P.ncols == n_want
             np.testing.assert_array_equal(lv.agg.cpu().numpy(), want)
-    _check_levels(h, dtype)
+    strength = [_host(lv.A) for lv in h.levels]
+    _check_levels(h, dtype, strength)
     st = h.stats()
     assert st["levels"] == len(h.levels) + 1 and st["products"] == len(h.levels)
     # numeric phases only, for new fine values
@@ -102,7 +105,7 @@ def test_hierarchy_levels(dtype):
     fine.val.mul_(0.5 + 1.5 * torch.rand(fine.val.shape, generator=g, device="cuda", dtype=dtype))
     fine.val.copy_(0.5 * (fine.val + _transpose_vals(fine)))     # keep it symmetric
     h.renumeric()
-    _check_levels(h, dtype)
+    _check_levels(h, dtype, strength)
     # the same from a CUDA graph after another rescale
     s = torch.cuda.Stream()
     s.wait_stream(torch.cuda.current_stream())
@@ -115,7 +118,7 @@ def test_hierarchy_levels(dtype):
     torch.cuda.current_stream().wait_stream(s)
     fine.val.mul_(1.25)
     graph.replay()
-    _check_levels(h, dtype)
+    _check_levels(h, dtype, strength)
     h.destroy()
 
 
