@@ -322,19 +322,19 @@ int ptap_aggregate(const ptap_csr* A, int32_t passes, int32_t rounds, int32_t* a
                    const ptap_allocator* alloc, void* stream);
 
 /* The smoothed prolongator of an aggregation: an opaque, library-owned
- * object holding the pattern of P = (I - omega D_F^-1 A_F) T, n x n_agg, with
+ * object holding the pattern of P = (I - omega D^-1 A_F) T, n x n_agg, with
  * sorted columns.  A_F is A filtered by strength: it keeps the diagonal and
  * the off-diagonal entries with |A(i,j)| >= theta * max_{k != i} |A(i,k)|
- * (0 <= theta <= 1; theta = 0 keeps every entry), and its diagonal D_F also
- * collects the dropped entries, so A_F 1 = A 1.  ptap_prolongator_symbolic
- * reads A (values too: the strong entries are settled here and kept, so the
- * pattern does not move with later values) and agg (copied); synchronises
- * `stream`.  ptap_prolongator_pattern returns its sizes and device pointers
- * (valid until destroy).  ptap_prolongator_numeric writes the nnz(P) values
- * P(i,a) = [agg(i) = a] - omega / D_F(i) * sum_{j in A_F(i,:), agg(j) = a}
- * A_F(i,j) into P_val (caller-owned device buffer of A's dtype); A must have
- * the pattern given at symbolic time (PTAP_ERR_PATTERN); asynchronous,
- * allocates nothing, and may be repeated whenever A's values change.
+ * (0 <= theta <= 1; theta = 0 keeps every entry); D = diag(A).
+ * ptap_prolongator_symbolic reads A (values too: the strong entries are
+ * settled here and kept, so the pattern does not move with later values)
+ * and agg (copied); synchronises `stream`.  ptap_prolongator_pattern returns
+ * its sizes and device pointers (valid until destroy).
+ * ptap_prolongator_numeric writes the nnz(P) values P(i,a) = [agg(i) = a] -
+ * omega / A(i,i) * sum_{j in A_F(i,:), agg(j) = a} A(i,j) into P_val
+ * (caller-owned device buffer of A's dtype); A must have the pattern given
+ * at symbolic time (PTAP_ERR_PATTERN); asynchronous, allocates nothing, and
+ * may be repeated whenever A's values change.
  * ptap_prolongator_check reads and clears its device status word
  * (PTAP_ERR_INVALID for a row without a diagonal entry).  Destroy frees it
  * (NULL is a no-op). */

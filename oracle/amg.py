@@ -17,9 +17,9 @@ on both sides is smoothed aggregation:
   reached; then up to ``rounds`` more rounds key the edges by the hash alone.  A pass turns pairs and lone nodes into the next pass's nodes,
   numbered by their smaller old node; ``passes`` passes give aggregates of at
   most 2^passes rows.
-* ``prolongator`` -- P = (I - omega D_F^-1 A_F) T with T(i, agg(i)) = 1 and
-  A_F the strength-filtered A (dropped entries lumped into its diagonal), on
-  the pattern of A_F T (structural: entries are kept when their value is 0).
+* ``prolongator`` -- P = (I - omega D^-1 A_F) T with T(i, agg(i)) = 1, A_F the
+  strength-filtered A and D = diag(A), on the pattern of A_F T (structural:
+  entries are kept when their value is 0).
 * ``greedy_matching`` -- an independent formulation of one pass run to
   convergence: sequential greedy matching over the edges in decreasing key
   order (the two agree when every edge has its own key).
@@ -122,12 +122,11 @@ def greedy_matching(A):
 
 
 def prolongator(A, agg, n_agg: int, omega: float = 2.0 / 3.0, theta: float = 0.0, S=None):
-    """P = (I - omega D_F^-1 A_F) T as (row_ptr, col_idx, val) on the pattern of A_F T.
+    """P = (I - omega D^-1 A_F) T as (row_ptr, col_idx, val) on the pattern of A_F T.
 
     A_F keeps the diagonal and the off-diagonal entries with |A(i,j)| >=
-    theta * max_{k != i} |A(i,k)|; the dropped entries are added to its
-    diagonal D_F (so A_F 1 = A 1).  Structural: entries are kept when their
-    value is zero.  S (A's pattern, other values) decides the strong entries
+    theta * max_{k != i} |A(i,k)|; D = diag(A).  Structural: entries are
+    kept when their value is zero.  S (A's pattern, other values) decides the strong entries
     instead of A when given: a hierarchy settles them once, at setup.
     """
     S = A if S is None else S
@@ -138,14 +137,10 @@ def prolongator(A, agg, n_agg: int, omega: float = 2.0 / 3.0, theta: float = 0.0
         off = [e for e in range(lo, hi) if int(A.col_idx[e]) != i]
         mx = max((abs(float(S.val[e])) for e in off), default=0.0)
         strong = [e for e in off if abs(float(S.val[e])) >= theta * mx]
-        sset = set(strong)
-        d = 0.0
-        for e in range(lo, hi):
-            if e not in sset:
-                d += float(A.val[e])
+        d = [float(A.val[e]) for e in range(lo, hi) if int(A.col_idx[e]) == i][0]
         cols = sorted({int(agg[int(A.col_idx[e])]) for e in strong} | {int(agg[i])})
         row = {c: 0.0 for c in cols}
-        row[int(agg[i])] = 1.0 - omega          # the diagonal term of A_F: omega * D_F / D_F
+        row[int(agg[i])] = 1.0 - omega          # the diagonal term: omega * A(i,i) / A(i,i)
         for e in strong:
             row[int(agg[int(A.col_idx[e])])] -= omega / d * float(A.val[e])
         ci_out.extend(cols)

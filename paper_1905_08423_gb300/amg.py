@@ -5,7 +5,7 @@ products C = P^T A P (Section 4.2.2, Tables 5-6), one per level, in the
 setup phase of its preconditioner, and repeats that setup as the operator's
 values change.  ``Hierarchy`` does the same on one GPU: per level it
 aggregates the rows (ptap_aggregate), forms the smoothed prolongator P =
-(I - omega D_F^-1 A_F) T, A_F the operator filtered by strength theta
+(I - omega D^-1 A_F) T, A_F the operator filtered by strength theta
 (ptap_prolongator_*; filtering keeps the coarse operators sparse, as the rows
 of Tables 5-6 are), and forms the next operator with
 ptap_symbolic / ptap_numeric; the coarse operator is the next level's A.

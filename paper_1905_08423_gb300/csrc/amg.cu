@@ -17,10 +17,11 @@
 //    nodes left unmatched stay alone.  Pass k matches the nodes of pass k-1,
 //    so `passes` passes give aggregates of at most 2^passes fine rows.
 //  * Tentative prolongator T(i, agg(i)) = 1 and the smoothed prolongator
-//    P = (I - omega D^-1 A) T: P(i, a) = [agg(i) = a] - omega / A(i,i) *
-//    sum over j in A(i,:) with agg(j) = a of A(i,j).  Its pattern is the
-//    pattern of A T (A holds its diagonal), formed by the library's row-wise
-//    symbolic product.
+//    P = (I - omega D^-1 A_F) T, A_F the diagonal and the strong entries of A
+//    (|A(i,j)| >= theta * max_{k != i} |A(i,k)|), D = diag(A):
+//    P(i, a) = [agg(i) = a] - omega / A(i,i) * sum over j in A_F(i,:) with
+//    agg(j) = a of A(i,j).  Its pattern is the pattern of A_F T, formed by the
+//    library's row-wise symbolic product.
 #include <algorithm>
 #include <new>
 #include <vector>
@@ -184,9 +185,11 @@ __global__ void k_filtered_fill(CsrI A, const uint8_t* __restrict__ mask, const 
   }
 }
 
-// Values of P = (I - omega D_F^-1 A_F) T on its sorted pattern, one thread a
-// row: A_F keeps the diagonal and the strong entries, and its diagonal D_F
-// also collects the weak entries (lumping), so A_F 1 = A 1.
+// Values of P = (I - omega D^-1 A_F) T on its sorted pattern, one thread a
+// row: A_F keeps the diagonal and the strong entries of A, D = diag(A).  The
+// weak entries are dropped, not lumped into the diagonal: on coarse levels,
+// whose off-diagonal entries take both signs, lumping can cancel most of the
+// diagonal and blow P's entries up.
 template <typename V>
 __global__ void k_prolong_values(CsrV<V> A, const uint8_t* __restrict__ mask, const int32_t* __restrict__ agg,
                                  const int32_t* __restrict__ prp, const int32_t* __restrict__ pci, double omega,
@@ -195,10 +198,11 @@ __global__ void k_prolong_values(CsrV<V> A, const uint8_t* __restrict__ mask, co
     const int32_t p0 = prp[i], p1 = prp[i + 1];
     V d = V(0);
     bool has_diag = false;
-    for (int32_t e = A.rp[i]; e < A.rp[i + 1]; ++e) {
-      if (A.ci[e] == i) has_diag = true;
-      if (!mask[e]) d += A.val[e];
-    }
+    for (int32_t e = A.rp[i]; e < A.rp[i + 1]; ++e)
+      if (A.ci[e] == i) {
+        has_diag = true;
+        d = A.val[e];
+      }
     for (int32_t q = p0; q < p1; ++q) pval[q] = V(0);
     auto pos = [&](int32_t a) {
       int32_t lo = p0, hi = p1;
@@ -214,7 +218,7 @@ __global__ void k_prolong_values(CsrV<V> A, const uint8_t* __restrict__ mask, co
       atomicExch(status, PTAP_ERR_INVALID);  // no diagonal entry, or the pattern is not this P's
       continue;
     }
-    pval[own] = V(1) - (V)omega;   // the filtered diagonal's own term: 1 - omega d / d
+    pval[own] = V(1) - (V)omega;   // the diagonal's own term: 1 - omega d / d
     const V f = (V)(omega) / d;
     for (int32_t e = A.rp[i]; e < A.rp[i + 1]; ++e) {
       if (!mask[e]) continue;

@@ -248,6 +248,7 @@ struct ClassArgs {
 };
 
 constexpr int kSigWarps = 4;
+constexpr uint32_t kMaxProbes = 256;  // linear probes of the class table before it counts as full
 
 struct SigSmem {
   __align__(16) uint8_t sig[kSigWarps][kFastSigCap];
@@ -280,6 +281,11 @@ __global__ void __launch_bounds__(kSigWarps * 32) k_class_build(ClassArgs c) {
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t mask = (1u << c.tlog2) - 1u;
   for (int64_t I = (int64_t)blockIdx.x * kSigWarps + w; I < c.n; I += (int64_t)gridDim.x * kSigWarps) {
+    // one row outside the limits, or a full table, sends the whole plan to the
+    // general kernel: nothing left to learn, so every warp stops
+    int stop = 0;
+    if (lane == 0) stop = ((volatile int32_t*)c.counters)[2] > 0 || ((volatile int32_t*)c.counters)[3] != 0;
+    if (__shfl_sync(0xffffffffu, stop, 0)) break;
     if (c.g.P.rp[I + 1] == c.g.P.rp[I]) {  // never visited
       if (lane == 0) c.row_class[I] = -1;
       continue;
@@ -296,7 +302,8 @@ __global__ void __launch_bounds__(kSigWarps * 32) k_class_build(ClassArgs c) {
     int role = 0;  // 1: this row publishes the key, 2: the key exists, 0: table full
     uint32_t slot = (uint32_t)(h >> 20) & mask;
     if (lane == 0) {
-      for (uint32_t probe = 0; probe <= mask; ++probe) {
+      // bounded probing: a table this crowded means far too many classes
+      for (uint32_t probe = 0; probe <= mask && probe < kMaxProbes; ++probe) {
         unsigned long long old = *(volatile unsigned long long*)&c.tkey[slot];
         if (old == kEmptyKey) old = atomicCAS(&c.tkey[slot], kEmptyKey, h);
         if (old == kEmptyKey) {
@@ -372,7 +379,7 @@ __global__ void __launch_bounds__(kSigWarps * 32) k_class_verify(ClassArgs c) {
       const unsigned long long h = sig_hash(sm.sig[w], len);
       uint32_t slot = (uint32_t)(h >> 20) & mask;
       int32_t found = -1;
-      for (uint32_t probe = 0; probe <= mask; ++probe) {
+      for (uint32_t probe = 0; probe <= mask && probe < kMaxProbes; ++probe) {
         const unsigned long long k = c.tkey[slot];
         if (k == h) {
           found = c.tcls[slot];

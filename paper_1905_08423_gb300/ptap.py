@@ -513,8 +513,8 @@ def aggregate(A: Csr, passes: int = 2, rounds: int = 16, stream=None):
 
 
 class Prolongator:
-    """ptap_prolongator_*: the pattern of P = (I - omega D_F^-1 A_F) T (A_F: A filtered by
-    strength theta, dropped entries lumped into its diagonal), and its values on demand."""
+    """ptap_prolongator_*: the pattern of P = (I - omega D^-1 A_F) T (A_F: A filtered by
+    strength theta, D = diag(A)), and its values on demand."""
 
     def __init__(self, A: Csr, agg: torch.Tensor, n_agg: int, theta: float = 0.0, stream=None):
         L = _lib()
