@@ -310,11 +310,11 @@ int ptap_scatter_add(const void* src, const int32_t* src_idx, const int32_t* dst
  * |A(i,j)| over their members; mutual picks are matched.  Rounds repeat until
  * none matches or `rounds` is reached; then up to `rounds` more rounds key
  * the edges by the hash alone (random priorities, which converge fast where
- * long chains of decreasing strength slow the first phase); unmatched nodes
- * stay alone.  Each of
- * `passes` (0..8) passes matches the previous pass's nodes, so aggregates
- * hold at most 2^passes rows.  Writes agg[i] (device, A.nrows entries,
- * caller-owned) in 0..*n_agg-1 and *n_agg (host).  Deterministic.
+ * long chains of decreasing strength slow the first phase).  A node still
+ * unmatched joins the pair with which it has the strongest edge, and stays
+ * alone only without a paired neighbour.  Each of `passes` (0..8) passes
+ * matches the previous pass's nodes.  Writes agg[i] (device, A.nrows
+ * entries, caller-owned) in 0..*n_agg-1 and *n_agg (host).  Deterministic.
  * Synchronises `stream`; scratch comes from `alloc` (NULL: cudaMallocAsync)
  * and is freed before return.  Errors: PTAP_ERR_INVALID, PTAP_ERR_OOM,
  * PTAP_ERR_CUDA. */

@@ -14,9 +14,11 @@ on both sides is smoothed aggregation:
   edge_hash(a, b), then the smaller node on a full tie), the strength of two
   nodes being the largest |A(i,j)| between their members; nodes that picked
   each other form a pair.  Rounds repeat until none pairs or ``rounds`` is
-  reached; then up to ``rounds`` more rounds key the edges by the hash alone.  A pass turns pairs and lone nodes into the next pass's nodes,
-  numbered by their smaller old node; ``passes`` passes give aggregates of at
-  most 2^passes rows.
+  reached; then up to ``rounds`` more rounds key the edges by the hash alone.
+  A node still unmatched joins the pair with which it has the strongest edge
+  (alone only without a paired neighbour).  A pass turns pairs (with what
+  joined them) and lone nodes into the next pass's nodes, numbered by their
+  smaller old node.
 * ``prolongator`` -- P = (I - omega D^-1 A_F) T with T(i, agg(i)) = 1, A_F the
   strength-filtered A and D = diag(A), on the pattern of A_F T (structural:
   entries are kept when their value is 0).
@@ -87,11 +89,22 @@ def aggregate(A, passes: int = 2, rounds: int = 16):
                         matched += a < b
                 if matched == 0:
                     break
-        leaders = [a for a in range(nn) if partner[a] < 0 or a < partner[a]]
+        # an unmatched node joins the pair it has the strongest edge with
+        att = [-1] * nn
+        for a in range(nn):
+            if partner[a] >= 0:
+                continue
+            cand = [(w, edge_hash(a, b), -b) for b, w in edges[a].items() if partner[b] >= 0]
+            if cand:
+                b = -max(cand)[2]
+                att[a] = min(b, partner[b])
+        leader = [min(a, partner[a]) if partner[a] >= 0 else (att[a] if att[a] >= 0 else a)
+                  for a in range(nn)]
+        leaders = [a for a in range(nn) if leader[a] == a]
         new_id = {a: k for k, a in enumerate(leaders)}
-        new_members = []
-        for a in leaders:
-            new_members.append(members[a] + (members[partner[a]] if partner[a] >= 0 else []))
+        new_members = [[] for _ in leaders]
+        for a in range(nn):
+            new_members[new_id[leader[a]]].extend(members[a])
         for k, mem in enumerate(new_members):
             for i in mem:
                 node_of[i] = k

@@ -14,8 +14,9 @@
 //    any order).  Rounds repeat until none matches or `rounds` is reached,
 //    then up to `rounds` more rounds key the edges by the hash alone (random
 //    priorities, which mop up what long chains of decreasing strength left);
-//    nodes left unmatched stay alone.  Pass k matches the nodes of pass k-1,
-//    so `passes` passes give aggregates of at most 2^passes fine rows.
+//    a node still unmatched joins the pair with which it has the strongest
+//    edge, and stays alone only without a paired neighbour.  Pass k matches
+//    the nodes of pass k-1.
 //  * Tentative prolongator T(i, agg(i)) = 1 and the smoothed prolongator
 //    P = (I - omega D^-1 A_F) T, A_F the diagonal and the strong entries of A
 //    (|A(i,j)| >= theta * max_{k != i} |A(i,k)|), D = diag(A):
@@ -96,23 +97,55 @@ __global__ void k_match(const int32_t* __restrict__ pick, int32_t nnodes, int32_
   }
 }
 
-// Leader of each new node: the smaller member of a pair, or a lone node.
-__global__ void k_leaders(const int32_t* __restrict__ partner, int32_t nnodes, int32_t* __restrict__ lead) {
+// A node left unmatched joins the pair with which it has the strongest edge
+// (same key as the picks); att[a] = that pair's leader (its smaller node),
+// or -1 if it has no matched neighbour (it then stays alone).  Without this a
+// node whose neighbours all paired off would stay a singleton level after
+// level, and coarsening would stall.
+template <typename V>
+__global__ void k_attach(CsrV<V> A, const int32_t* __restrict__ node_of, const int32_t* __restrict__ mem_ptr,
+                         const int32_t* __restrict__ members, int32_t nnodes, const int32_t* __restrict__ partner,
+                         int32_t* __restrict__ att) {
   for (int32_t a = blockIdx.x * blockDim.x + threadIdx.x; a < nnodes; a += gridDim.x * blockDim.x) {
-    const int32_t b = partner[a];
-    lead[a] = (b < 0 || a < b) ? 1 : 0;
+    int32_t best = -1;
+    double bw = -1.0;
+    uint32_t bh = 0;
+    if (partner[a] < 0) {
+      for (int32_t m = mem_ptr[a]; m < mem_ptr[a + 1]; ++m) {
+        const int32_t i = members[m];
+        for (int32_t e = A.rp[i]; e < A.rp[i + 1]; ++e) {
+          const int32_t b = node_of[A.ci[e]];
+          if (b == a || partner[b] < 0) continue;
+          const double w = fabs((double)A.val[e]);
+          const uint32_t h = edge_hash(a, b);
+          if (stronger(w, h, bw, bh) || (w == bw && h == bh && b < best)) {
+            best = b;
+            bw = w;
+            bh = h;
+          }
+        }
+      }
+    }
+    att[a] = best < 0 ? -1 : min(best, partner[best]);
   }
 }
 
-// New node id of every old node (pairs share their leader's id), the fine
-// rows' new node, and the new member lists (ordered by old node, then member).
-__global__ void k_relabel(const int32_t* __restrict__ partner, const int32_t* __restrict__ lead_pos,
-                          int32_t nnodes, int32_t* __restrict__ new_of_old) {
-  for (int32_t a = blockIdx.x * blockDim.x + threadIdx.x; a < nnodes; a += gridDim.x * blockDim.x) {
-    const int32_t b = partner[a];
-    const int32_t l = (b < 0 || a < b) ? a : b;
-    new_of_old[a] = lead_pos[l];
-  }
+__device__ __forceinline__ int32_t leader_of(int32_t a, const int32_t* partner, const int32_t* att) {
+  const int32_t b = partner[a];
+  return b >= 0 ? min(a, b) : (att[a] >= 0 ? att[a] : a);
+}
+
+// New nodes: pair leaders and nodes that stayed alone, in order of old id.
+__global__ void k_leaders(const int32_t* __restrict__ partner, const int32_t* __restrict__ att, int32_t nnodes,
+                          int32_t* __restrict__ lead) {
+  for (int32_t a = blockIdx.x * blockDim.x + threadIdx.x; a < nnodes; a += gridDim.x * blockDim.x)
+    lead[a] = leader_of(a, partner, att) == a ? 1 : 0;
+}
+
+__global__ void k_relabel(const int32_t* __restrict__ partner, const int32_t* __restrict__ att,
+                          const int32_t* __restrict__ lead_pos, int32_t nnodes, int32_t* __restrict__ new_of_old) {
+  for (int32_t a = blockIdx.x * blockDim.x + threadIdx.x; a < nnodes; a += gridDim.x * blockDim.x)
+    new_of_old[a] = lead_pos[leader_of(a, partner, att)];
 }
 
 __global__ void k_map_rows(int32_t n, const int32_t* __restrict__ old_node, const int32_t* __restrict__ new_of_old,
@@ -121,27 +154,21 @@ __global__ void k_map_rows(int32_t n, const int32_t* __restrict__ old_node, cons
     new_node[i] = new_of_old[old_node[i]];
 }
 
-// Members of the new nodes: the leader's members, then its partner's.
-__global__ void k_new_members(const int32_t* __restrict__ partner, const int32_t* __restrict__ lead_pos,
-                              int32_t nnodes, const int32_t* __restrict__ mem_ptr,
-                              const int32_t* __restrict__ members, const int32_t* __restrict__ new_ptr,
-                              int32_t* __restrict__ new_members) {
-  for (int32_t a = blockIdx.x * blockDim.x + threadIdx.x; a < nnodes; a += gridDim.x * blockDim.x) {
-    const int32_t b = partner[a];
-    if (!(b < 0 || a < b)) continue;
-    int32_t o = new_ptr[lead_pos[a]];
-    for (int32_t m = mem_ptr[a]; m < mem_ptr[a + 1]; ++m) new_members[o++] = members[m];
-    if (b >= 0)
-      for (int32_t m = mem_ptr[b]; m < mem_ptr[b + 1]; ++m) new_members[o++] = members[m];
-  }
+__global__ void k_new_sizes(const int32_t* __restrict__ new_of_old, int32_t nnodes,
+                            const int32_t* __restrict__ mem_ptr, int32_t* __restrict__ size) {
+  for (int32_t a = blockIdx.x * blockDim.x + threadIdx.x; a < nnodes; a += gridDim.x * blockDim.x)
+    atomicAdd(&size[new_of_old[a]], mem_ptr[a + 1] - mem_ptr[a]);
 }
 
-__global__ void k_new_sizes(const int32_t* __restrict__ partner, const int32_t* __restrict__ lead_pos,
-                            int32_t nnodes, const int32_t* __restrict__ mem_ptr, int32_t* __restrict__ size) {
+// Members of the new nodes (their order inside a node does not matter: the
+// picks take a strict maximum).
+__global__ void k_new_members(const int32_t* __restrict__ new_of_old, int32_t nnodes,
+                              const int32_t* __restrict__ mem_ptr, const int32_t* __restrict__ members,
+                              int32_t* __restrict__ cursor, int32_t* __restrict__ new_members) {
   for (int32_t a = blockIdx.x * blockDim.x + threadIdx.x; a < nnodes; a += gridDim.x * blockDim.x) {
-    const int32_t b = partner[a];
-    if (!(b < 0 || a < b)) continue;
-    size[lead_pos[a]] = (mem_ptr[a + 1] - mem_ptr[a]) + (b >= 0 ? mem_ptr[b + 1] - mem_ptr[b] : 0);
+    const int32_t cnt = mem_ptr[a + 1] - mem_ptr[a];
+    int32_t o = atomicAdd(&cursor[new_of_old[a]], cnt);
+    for (int32_t m = mem_ptr[a]; m < mem_ptr[a + 1]; ++m) new_members[o++] = members[m];
   }
 }
 
@@ -260,7 +287,7 @@ int aggregate_t(const ptap_csr* Ain, int32_t passes, int32_t rounds, int32_t* ag
   Scratch sc(&mem);
   int32_t *node_of = nullptr, *mem_ptr = nullptr, *members = nullptr, *partner = nullptr, *pick = nullptr,
           *counter = nullptr, *lead = nullptr, *lead_pos = nullptr, *new_of_old = nullptr, *size = nullptr,
-          *new_ptr = nullptr, *new_members = nullptr;
+          *new_ptr = nullptr, *new_members = nullptr, *att = nullptr;
   PTAP_TRY(sc.get(&node_of, std::max(n, 1)));
   PTAP_TRY(sc.get(&mem_ptr, (int64_t)n + 1));
   PTAP_TRY(sc.get(&members, std::max(n, 1)));
@@ -273,6 +300,7 @@ int aggregate_t(const ptap_csr* Ain, int32_t passes, int32_t rounds, int32_t* ag
   PTAP_TRY(sc.get(&size, (int64_t)n + 1));
   PTAP_TRY(sc.get(&new_ptr, (int64_t)n + 1));
   PTAP_TRY(sc.get(&new_members, std::max(n, 1)));
+  PTAP_TRY(sc.get(&att, (int64_t)n + 1));  // attachments, then the member cursor of each new node
   // pass 0 nodes: the fine rows themselves
   k_iota<<<grid_of(n + 1), 256, 0, s>>>(n, mem_ptr);
   k_iota<<<grid_of(n), 256, 0, s>>>(n - 1, members);
@@ -297,18 +325,21 @@ int aggregate_t(const ptap_csr* Ain, int32_t passes, int32_t rounds, int32_t* ag
         r = rounds - 1;  // on to the hash-keyed rounds
       }
     }
-    // new nodes: leaders in order of their old id
-    k_leaders<<<grid_of(nnodes), 256, 0, s>>>(partner, nnodes, lead);
+    // unmatched nodes join their strongest neighbouring pair; new nodes are
+    // the pair leaders and the nodes left alone, in order of their old id
+    k_attach<V><<<grid_of(nnodes), 256, 0, s>>>(A, node_of, mem_ptr, members, nnodes, partner, att);
+    k_leaders<<<grid_of(nnodes), 256, 0, s>>>(partner, att, nnodes, lead);
     PTAP_LAUNCHED();
     int64_t nnew = 0;
     PTAP_TRY(exclusive_scan(mem, lead, lead_pos, nnodes, &nnew, s));
-    k_relabel<<<grid_of(nnodes), 256, 0, s>>>(partner, lead_pos, nnodes, new_of_old);
+    k_relabel<<<grid_of(nnodes), 256, 0, s>>>(partner, att, lead_pos, nnodes, new_of_old);
     k_map_rows<<<grid_of(n), 256, 0, s>>>(n, node_of, new_of_old, node_of);
-    k_new_sizes<<<grid_of(nnodes), 256, 0, s>>>(partner, lead_pos, nnodes, mem_ptr, size);
+    PTAP_CUDA(cudaMemsetAsync(size, 0, (size_t)(nnew + 1) * sizeof(int32_t), s));
+    k_new_sizes<<<grid_of(nnodes), 256, 0, s>>>(new_of_old, nnodes, mem_ptr, size);
     PTAP_LAUNCHED();
     PTAP_TRY(exclusive_scan(mem, size, new_ptr, nnew, nullptr, s));
-    k_new_members<<<grid_of(nnodes), 256, 0, s>>>(partner, lead_pos, nnodes, mem_ptr, members, new_ptr,
-                                                  new_members);
+    PTAP_CUDA(cudaMemcpyAsync(att, new_ptr, (size_t)nnew * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+    k_new_members<<<grid_of(nnodes), 256, 0, s>>>(new_of_old, nnodes, mem_ptr, members, att, new_members);
     PTAP_LAUNCHED();
     std::swap(mem_ptr, new_ptr);
     std::swap(members, new_members);
