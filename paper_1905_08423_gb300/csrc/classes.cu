@@ -28,7 +28,10 @@
 // byte by byte with the pool entry of its hash -- at once when the entry is
 // ready, otherwise in a short second pass -- so a hash collision can only
 // demote rows to the general path, never corrupt results.  No warp waits on
-// another.
+// another.  In front of it sits a table of row shapes (the patterns a
+// program depends on, relative to the row's first coarse column): a row
+// whose shape was seen takes that shape's class without computing its
+// program (k_class_build).
 #include <algorithm>
 #include <vector>
 
@@ -241,20 +244,91 @@ struct ClassArgs {
   int64_t pool_cap;
   int32_t* class_off;        // [K+1] pool offset per class (class_off[k] = start)
   int32_t* counters;         // [0] classes, [1] pool bytes used, [2] slow rows, [3] overflow,
-                             // [4] rows left to verify
+                             // [4] rows left to verify, [5] shape pool words used
   int32_t* row_class;        // per fine row: class id, or -1 (no P entries), or -2 (general
                              // path), or -3 (to be verified by k_class_verify)
   int32_t* status;
+  // the shape table (see k_class_build): keys, ready flags, class of each
+  // shape, and the shape pool (int32 words); counters[5] counts pool words
+  unsigned long long* skey;
+  int32_t* sready;
+  int32_t* scls;
+  int32_t* spool;
+  int32_t* soff;             // pool offset of each slot's shape
+  int64_t spool_cap;
 };
 
 constexpr int kSigWarps = 4;
 constexpr uint32_t kMaxProbes = 256;  // linear probes of the class table before it counts as full
 
+constexpr int kShapeCap = 512;       // words of a row's shape kept on chip; longer rows skip the shape table
+
 struct SigSmem {
   __align__(16) uint8_t sig[kSigWarps][kFastSigCap];
   int32_t cand[kSigWarps][kFastMaxT];
   int32_t keys[kSigWarps][kFastMaxT];
+  int32_t shape[kSigWarps][kShapeCap];
 };
+
+// The shape of fine row I: everything its program depends on, relative to
+// c = the first column of P(I,:):
+//   na, pI, (P.ci of P(I,:)) - c, then per entry a of A(I,:): pa, (columns of
+//   P(k_a,:)) - c, then per entry s of P(I,:): L = length of C row i_s and
+//   (its columns) - c.
+// Two rows with equal shapes have equal programs: the slots of A P follow
+// from the order of the relative columns, the positions in C from the
+// relative C rows.  Returns the length in words; -1 if the row is outside
+// the fast-path limits (as compute_sig would find, except the row of A P
+// being too long, which its program reveals); -4 if the shape exceeds the
+// on-chip buffer.
+__device__ int compute_shape(const SigGeom& g, int32_t I, int32_t* sh) {
+  const int lane = threadIdx.x & 31;
+  const int32_t a0 = g.A.rp[I], na = g.A.rp[I + 1] - a0;
+  const int32_t p0 = g.P.rp[I], pI = g.P.rp[I + 1] - p0;
+  if (na > kFastMaxA || pI > kFastMaxP || pI <= 0) return -1;
+  const int32_t base = g.P.ci[p0];
+  int32_t pb = 0, pa = 0;
+  if (lane < na) {
+    const int32_t k = g.A.ci[a0 + lane];
+    pb = g.P.rp[k];
+    pa = g.P.rp[k + 1] - pb;
+  }
+  if (__any_sync(0xffffffffu, pa > kFastMaxB)) return -1;
+  int32_t off = 1 + pa;  // inclusive scan of 1 + pa over the entries of A(I,:)
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const int32_t y = __shfl_up_sync(0xffffffffu, off, d);
+    if (lane >= d) off += y;
+  }
+  const int32_t asec = __shfl_sync(0xffffffffu, off, 31);  // words of the A section
+  int len = 2 + pI + asec;
+  if (len > kShapeCap) return -4;
+  if (lane == 0) {
+    sh[0] = na;
+    sh[1] = pI;
+  }
+  if (lane < pI) sh[2 + lane] = g.P.ci[p0 + lane] - base;
+  if (lane < na) {
+    int32_t o = 2 + pI + off - (1 + pa);
+    sh[o] = pa;
+    for (int32_t b = 0; b < pa; ++b) sh[o + 1 + b] = g.P.ci[pb + b] - base;
+  }
+  for (int32_t s = 0; s < pI; ++s) {
+    const int32_t i = g.P.ci[p0 + s];
+    const int32_t c0 = g.C.rp[i], L = g.C.rp[i + 1] - c0;  // the same in every lane
+    if (L > 255) return -1;
+    if (len + 1 + L > kShapeCap) return -4;
+    if (lane == 0) sh[len] = L;
+    for (int32_t j = lane; j < L; j += 32) sh[len + 1 + j] = g.C.ci[c0 + j] - base;
+    len += 1 + L;
+  }
+  __syncwarp();
+  return len;
+}
+
+// Order-sensitive 64-bit hash of the words w[0, len), warp-cooperative.
+__device__ unsigned long long words_hash(const int32_t* w, int len);
+
 
 // Byte-compares the warp's signature sig[0, len) with the pool entry of class
 // cls; reads bypass L1 (entries may have been written by another SM during
@@ -269,17 +343,130 @@ __device__ bool same_program(const ClassArgs& c, int32_t cls, const uint8_t* sig
   return __all_sync(0xffffffffu, same);
 }
 
-// One pass over the fine rows: each row's signature is hashed into the table.
-// The row that inserts a key publishes its program to the pool and then sets
-// the slot's ready flag; a row that finds its key already ready compares its
-// signature with the published bytes at once.  A row whose key is not yet
-// ready (its publisher is still writing, on another SM) is marked -3 and
-// checked by k_class_verify after this launch.  Nothing waits on another
-// warp; a 64-bit hash collision can only send rows to the general path.
+__device__ unsigned long long words_hash(const int32_t* w, int len) {
+  const int lane = threadIdx.x & 31;
+  unsigned long long h = 0x84222325cbf29ce4ull ^ mix64((unsigned long long)(lane + 1) * 0x9e3779b97f4a7c15ull);
+  for (int x = lane; x < len; x += 32) h = (h ^ (unsigned long long)(uint32_t)w[x]) * 0x100000001b3ull;
+  h = mix64(h + (unsigned long long)lane * 0x632be59bd9b4e019ull + (unsigned long long)len);
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) h ^= __shfl_xor_sync(0xffffffffu, h, d);
+  return h == kEmptyKey ? 0 : h;
+}
+
+// Class of the program sig[0, len) in the program table: the row that
+// inserts a key publishes its program to the pool and then sets the slot's
+// ready flag; a row that finds its key ready compares its program with the
+// published bytes.  Returns the class id, -2 (table or pool full, or a hash
+// collision: the general path) or -3 (the key's program not yet published;
+// k_class_verify settles the row after this launch).  No warp waits.
+__device__ int32_t program_class(const ClassArgs& c, const uint8_t* sig, int len) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t mask = (1u << c.tlog2) - 1u;
+  const unsigned long long h = sig_hash(sig, len);
+  int role = 0;  // 1: this row publishes the key, 2: the key exists, 0: table full
+  uint32_t slot = (uint32_t)(h >> 20) & mask;
+  if (lane == 0) {
+    // bounded probing: a table this crowded means far too many classes
+    for (uint32_t probe = 0; probe <= mask && probe < kMaxProbes; ++probe) {
+      unsigned long long old = *(volatile unsigned long long*)&c.tkey[slot];
+      if (old == kEmptyKey) old = atomicCAS(&c.tkey[slot], kEmptyKey, h);
+      if (old == kEmptyKey) {
+        role = 1;
+        break;
+      }
+      if (old == h) {
+        role = 2;
+        break;
+      }
+      slot = (slot + 1) & mask;
+    }
+    if (role == 0) atomicExch(&c.counters[3], 1);
+  }
+  role = __shfl_sync(0xffffffffu, role, 0);
+  slot = __shfl_sync(0xffffffffu, slot, 0);
+  int32_t cls = -2;
+  if (role == 1) {
+    int32_t off = 0;
+    if (lane == 0) {
+      off = atomicAdd(&c.counters[1], len);
+      if ((int64_t)off + len <= c.pool_cap) {
+        cls = atomicAdd(&c.counters[0], 1);
+        c.class_off[cls] = off;
+      } else {
+        cls = -1;
+        atomicExch(&c.counters[3], 1);
+      }
+    }
+    cls = __shfl_sync(0xffffffffu, cls, 0);
+    off = __shfl_sync(0xffffffffu, off, 0);
+    if (cls >= 0)
+      for (int x = lane; x < len; x += 32) c.pool[off + x] = sig[x];
+    __syncwarp();
+    if (lane == 0) {
+      c.tcls[slot] = cls;
+      __threadfence();  // the program and its class id before the flag
+      atomicExch(&c.tready[slot], 1);
+    }
+    if (cls < 0) cls = -2;
+  } else if (role == 2) {
+    int ready = 0;
+    if (lane == 0) ready = atomicAdd(&c.tready[slot], 0);
+    ready = __shfl_sync(0xffffffffu, ready, 0);
+    __threadfence();
+    if (ready) {
+      const int32_t k = __ldcg(&c.tcls[slot]);
+      cls = (k >= 0 && same_program(c, k, sig, len)) ? k : -2;
+    } else {
+      cls = -3;
+    }
+  }
+  return cls;
+}
+
+// The class of a row from its program (the full path).
+__device__ int32_t row_program_class(const ClassArgs& c, int32_t I, SigSmem& sm, int w) {
+  const int len = compute_sig(c.g, I, sm.sig[w], sm.cand[w], sm.keys[w], c.status);
+  return len < 0 ? -2 : program_class(c, sm.sig[w], len);
+}
+
+// Probes the shape table for the key h: 1 = this row inserted it, 2 = it
+// exists, 0 = no room (the row takes the full path).  *slot gets the slot.
+__device__ int shape_probe(const ClassArgs& c, unsigned long long h, uint32_t* slot_out) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t mask = (1u << c.tlog2) - 1u;
+  uint32_t slot = (uint32_t)(h >> 24) & mask;
+  int role = 0;
+  if (lane == 0) {
+    for (uint32_t probe = 0; probe <= mask && probe < kMaxProbes; ++probe) {
+      unsigned long long old = *(volatile unsigned long long*)&c.skey[slot];
+      if (old == kEmptyKey) old = atomicCAS(&c.skey[slot], kEmptyKey, h);
+      if (old == kEmptyKey) {
+        role = 1;
+        break;
+      }
+      if (old == h) {
+        role = 2;
+        break;
+      }
+      slot = (slot + 1) & mask;
+    }
+  }
+  *slot_out = __shfl_sync(0xffffffffu, slot, 0);
+  return __shfl_sync(0xffffffffu, role, 0);
+}
+
+// One pass over the fine rows.  Most rows of a mesh operator repeat the
+// structure of their neighbours, shifted: a row first computes its shape
+// (compute_shape: loads only, no sorting or searching) and looks it up in
+// the shape table.  The row that inserts a shape computes the program once,
+// finds its class in the program table and publishes the shape with that
+// class; later rows with an equal shape (compared word by word) take the
+// class directly.  Rows whose shape is still being published, or whose
+// shape does not fit on chip, compute their program themselves.  Nothing
+// waits on another warp; a hash collision can only cost a row the shortcut.
 __global__ void __launch_bounds__(kSigWarps * 32) k_class_build(ClassArgs c) {
   __shared__ SigSmem sm;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const uint32_t mask = (1u << c.tlog2) - 1u;
   for (int64_t I = (int64_t)blockIdx.x * kSigWarps + w; I < c.n; I += (int64_t)gridDim.x * kSigWarps) {
     // one row outside the limits, or a full table, sends the whole plan to the
     // general kernel: nothing left to learn, so every warp stops
@@ -290,70 +477,53 @@ __global__ void __launch_bounds__(kSigWarps * 32) k_class_build(ClassArgs c) {
       if (lane == 0) c.row_class[I] = -1;
       continue;
     }
-    const int len = compute_sig(c.g, (int32_t)I, sm.sig[w], sm.cand[w], sm.keys[w], c.status);
-    if (len < 0) {
-      if (lane == 0) {
-        c.row_class[I] = -2;
-        atomicAdd(&c.counters[2], 1);
-      }
-      continue;
-    }
-    const unsigned long long h = sig_hash(sm.sig[w], len);
-    int role = 0;  // 1: this row publishes the key, 2: the key exists, 0: table full
-    uint32_t slot = (uint32_t)(h >> 20) & mask;
-    if (lane == 0) {
-      // bounded probing: a table this crowded means far too many classes
-      for (uint32_t probe = 0; probe <= mask && probe < kMaxProbes; ++probe) {
-        unsigned long long old = *(volatile unsigned long long*)&c.tkey[slot];
-        if (old == kEmptyKey) old = atomicCAS(&c.tkey[slot], kEmptyKey, h);
-        if (old == kEmptyKey) {
-          role = 1;
-          break;
-        }
-        if (old == h) {
-          role = 2;
-          break;
-        }
-        slot = (slot + 1) & mask;
-      }
-      if (role == 0) atomicExch(&c.counters[3], 1);
-    }
-    role = __shfl_sync(0xffffffffu, role, 0);
-    slot = __shfl_sync(0xffffffffu, slot, 0);
+    int32_t* sh = sm.shape[w];
+    const int slen = compute_shape(c.g, (int32_t)I, sh);
     int32_t cls = -2;
-    if (role == 1) {
-      int32_t off = 0;
-      if (lane == 0) {
-        off = atomicAdd(&c.counters[1], len);
-        if ((int64_t)off + len <= c.pool_cap) {
-          cls = atomicAdd(&c.counters[0], 1);
-          c.class_off[cls] = off;
-        } else {
-          cls = -1;
-          atomicExch(&c.counters[3], 1);
+    if (slen == -1) {
+      cls = -2;  // outside the limits
+    } else if (slen < 0) {
+      cls = row_program_class(c, (int32_t)I, sm, w);
+    } else {
+      const unsigned long long h = words_hash(sh, slen);
+      uint32_t slot = 0;
+      const int role = shape_probe(c, h, &slot);
+      if (role == 1) {
+        cls = row_program_class(c, (int32_t)I, sm, w);
+        int32_t off = -1;
+        if (lane == 0) {
+          off = (int32_t)atomicAdd(&c.counters[5], slen);
+          if ((int64_t)off + slen > c.spool_cap) off = -1;
         }
-      }
-      cls = __shfl_sync(0xffffffffu, cls, 0);
-      off = __shfl_sync(0xffffffffu, off, 0);
-      if (cls >= 0)
-        for (int x = lane; x < len; x += 32) c.pool[off + x] = sm.sig[w][x];
-      __syncwarp();
-      if (lane == 0) {
-        c.tcls[slot] = cls;
-        __threadfence();  // the program and its class id before the flag
-        atomicExch(&c.tready[slot], 1);
-      }
-      if (cls < 0) cls = -2;
-    } else if (role == 2) {
-      int ready = 0;
-      if (lane == 0) ready = atomicAdd(&c.tready[slot], 0);
-      ready = __shfl_sync(0xffffffffu, ready, 0);
-      __threadfence();
-      if (ready) {
-        const int32_t k = __ldcg(&c.tcls[slot]);
-        cls = (k >= 0 && same_program(c, k, sm.sig[w], len)) ? k : -2;
+        off = __shfl_sync(0xffffffffu, off, 0);
+        if (off >= 0)
+          for (int x = lane; x < slen; x += 32) c.spool[off + x] = sh[x];
+        __syncwarp();
+        if (lane == 0) {
+          c.soff[slot] = off;
+          c.scls[slot] = cls;
+          __threadfence();  // the shape, its offset and class before the flag
+          atomicExch(&c.sready[slot], 1);
+        }
+      } else if (role == 2) {
+        int ready = 0;
+        if (lane == 0) ready = atomicAdd(&c.sready[slot], 0);
+        ready = __shfl_sync(0xffffffffu, ready, 0);
+        __threadfence();
+        bool same = false;
+        int32_t k = -2;
+        if (ready) {
+          const int32_t off = __ldcg(&c.soff[slot]);
+          k = __ldcg(&c.scls[slot]);
+          if (off >= 0 && __ldcg(&c.spool[off]) == sh[0]) {
+            same = true;
+            for (int x = lane; x < slen; x += 32) same = same && __ldcg(&c.spool[off + x]) == sh[x];
+            same = __all_sync(0xffffffffu, same);
+          }
+        }
+        cls = (same && k != -3) ? k : row_program_class(c, (int32_t)I, sm, w);
       } else {
-        cls = -3;
+        cls = row_program_class(c, (int32_t)I, sm, w);
       }
     }
     if (lane == 0) {
@@ -365,8 +535,6 @@ __global__ void __launch_bounds__(kSigWarps * 32) k_class_build(ClassArgs c) {
   }
 }
 
-// The rows k_class_build could not check yet: signature again, compared with
-// the (now complete) pool entry of its key.
 __global__ void __launch_bounds__(kSigWarps * 32) k_class_verify(ClassArgs c) {
   __shared__ SigSmem sm;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -550,6 +718,17 @@ int build_classes(ptap_plan* p, const ptap_csr* A, const ptap_csr* P, cudaStream
   PTAP_TRY(sc.get(&row_class, p->n));
   PTAP_TRY(sc.get(&class_off, tcap + 1));
   PTAP_TRY(sc.get(&pool, pool_cap));
+  // the shape table in front of the program table (k_class_build)
+  const int64_t spool_cap = (int64_t)1 << 22;
+  unsigned long long* skey = nullptr;
+  int32_t *sready = nullptr, *scls = nullptr, *soff = nullptr, *spool = nullptr;
+  PTAP_TRY(sc.get(&skey, tcap));
+  PTAP_TRY(sc.get(&sready, tcap));
+  PTAP_TRY(sc.get(&scls, tcap));
+  PTAP_TRY(sc.get(&soff, tcap));
+  PTAP_TRY(sc.get(&spool, spool_cap));
+  PTAP_CUDA(cudaMemsetAsync(skey, 0xff, tcap * sizeof(unsigned long long), s));
+  PTAP_CUDA(cudaMemsetAsync(sready, 0, tcap * sizeof(int32_t), s));
   PTAP_CUDA(cudaMemsetAsync(tkey, 0xff, tcap * sizeof(unsigned long long), s));
   PTAP_CUDA(cudaMemsetAsync(tready, 0, tcap * sizeof(int32_t), s));
   PTAP_CUDA(cudaMemsetAsync(counters, 0, 8 * sizeof(int32_t), s));
@@ -567,6 +746,12 @@ int build_classes(ptap_plan* p, const ptap_csr* A, const ptap_csr* P, cudaStream
   c.counters = counters;
   c.row_class = row_class;
   c.status = p->status;
+  c.skey = skey;
+  c.sready = sready;
+  c.scls = scls;
+  c.spool = spool;
+  c.soff = soff;
+  c.spool_cap = spool_cap;
   // latency-bound warp-per-row work: fill the SMs (16 CTAs of 4 warps each)
   const int grid = num_sms() * 16;
   PhaseRange r_build("ptap: class signatures", s);
