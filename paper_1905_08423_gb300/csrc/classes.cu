@@ -267,7 +267,7 @@ struct SigSmem {
   __align__(16) uint8_t sig[kSigWarps][kFastSigCap];
   int32_t cand[kSigWarps][kFastMaxT];
   int32_t keys[kSigWarps][kFastMaxT];
-  int32_t shape[kSigWarps][kShapeCap];
+  int32_t shape[kSigWarps][3][kShapeCap];  // per warp: the row's shape and two remembered ones
 };
 
 // The shape of fine row I: everything its program depends on, relative to
@@ -467,71 +467,121 @@ __device__ int shape_probe(const ClassArgs& c, unsigned long long h, uint32_t* s
 __global__ void __launch_bounds__(kSigWarps * 32) k_class_build(ClassArgs c) {
   __shared__ SigSmem sm;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int64_t I = (int64_t)blockIdx.x * kSigWarps + w; I < c.n; I += (int64_t)gridDim.x * kSigWarps) {
-    // one row outside the limits, or a full table, sends the whole plan to the
-    // general kernel: nothing left to learn, so every warp stops
-    int stop = 0;
-    if (lane == 0) stop = ((volatile int32_t*)c.counters)[2] > 0 || ((volatile int32_t*)c.counters)[3] != 0;
-    if (__shfl_sync(0xffffffffu, stop, 0)) break;
-    if (c.g.P.rp[I + 1] == c.g.P.rp[I]) {  // never visited
-      if (lane == 0) c.row_class[I] = -1;
-      continue;
-    }
-    int32_t* sh = sm.shape[w];
-    const int slen = compute_shape(c.g, (int32_t)I, sh);
-    int32_t cls = -2;
-    if (slen == -1) {
-      cls = -2;  // outside the limits
-    } else if (slen < 0) {
-      cls = row_program_class(c, (int32_t)I, sm, w);
-    } else {
-      const unsigned long long h = words_hash(sh, slen);
-      uint32_t slot = 0;
-      const int role = shape_probe(c, h, &slot);
-      if (role == 1) {
+  // Each warp takes runs of 32 consecutive fine rows, where neighbouring rows
+  // repeat a few shapes, and remembers the last two shapes it resolved (with
+  // their classes) in shared memory: most rows match one of them there, with
+  // no global atomic and no read of the shared pools.
+  int buf = 0;                          // which of the three buffers holds this row's shape
+  int memo[2] = {1, 2};                 // buffers of the remembered shapes, most recent first
+  unsigned long long memo_h[2] = {kEmptyKey, kEmptyKey};
+  int32_t memo_len[2] = {0, 0}, memo_cls[2] = {-2, -2};
+  const int64_t warps = (int64_t)gridDim.x * kSigWarps;
+  for (int64_t run = (int64_t)blockIdx.x * kSigWarps + w; run * 32 < c.n; run += warps) {
+    const int64_t I1 = min((int64_t)c.n, run * 32 + 32);
+    for (int64_t I = run * 32; I < I1; ++I) {
+      // one row outside the limits, or a full table, sends the whole plan to the
+      // general kernel: nothing left to learn, so every warp stops
+      int stop = 0;
+      if (lane == 0) stop = ((volatile int32_t*)c.counters)[2] > 0 || ((volatile int32_t*)c.counters)[3] != 0;
+      if (__shfl_sync(0xffffffffu, stop, 0)) return;
+      if (c.g.P.rp[I + 1] == c.g.P.rp[I]) {  // never visited
+        if (lane == 0) c.row_class[I] = -1;
+        continue;
+      }
+      int32_t* sh = sm.shape[w][buf];
+      const int slen = compute_shape(c.g, (int32_t)I, sh);
+      int32_t cls = -2;
+      if (slen == -1) {
+        cls = -2;  // outside the limits
+      } else if (slen < 0) {
         cls = row_program_class(c, (int32_t)I, sm, w);
-        int32_t off = -1;
-        if (lane == 0) {
-          off = (int32_t)atomicAdd(&c.counters[5], slen);
-          if ((int64_t)off + slen > c.spool_cap) off = -1;
+      } else {
+        const unsigned long long h = words_hash(sh, slen);
+        int hit = -1;
+        for (int q = 0; q < 2 && hit < 0; ++q) {
+          if (memo_h[q] != h || memo_len[q] != slen) continue;
+          const int32_t* m = sm.shape[w][memo[q]];
+          bool same = true;
+          for (int x = lane; x < slen; x += 32) same = same && m[x] == sh[x];
+          if (__all_sync(0xffffffffu, same)) hit = q;
         }
-        off = __shfl_sync(0xffffffffu, off, 0);
-        if (off >= 0)
-          for (int x = lane; x < slen; x += 32) c.spool[off + x] = sh[x];
-        __syncwarp();
-        if (lane == 0) {
-          c.soff[slot] = off;
-          c.scls[slot] = cls;
-          __threadfence();  // the shape, its offset and class before the flag
-          atomicExch(&c.sready[slot], 1);
-        }
-      } else if (role == 2) {
-        int ready = 0;
-        if (lane == 0) ready = atomicAdd(&c.sready[slot], 0);
-        ready = __shfl_sync(0xffffffffu, ready, 0);
-        __threadfence();
-        bool same = false;
-        int32_t k = -2;
-        if (ready) {
-          const int32_t off = __ldcg(&c.soff[slot]);
-          k = __ldcg(&c.scls[slot]);
-          if (off >= 0 && __ldcg(&c.spool[off]) == sh[0]) {
-            same = true;
-            for (int x = lane; x < slen; x += 32) same = same && __ldcg(&c.spool[off + x]) == sh[x];
-            same = __all_sync(0xffffffffu, same);
+        if (hit >= 0) {
+          cls = memo_cls[hit];
+          if (hit == 1) {  // most recent first
+            const int tb = memo[0];
+            memo[0] = memo[1];
+            memo[1] = tb;
+            const unsigned long long th = memo_h[0];
+            memo_h[0] = memo_h[1];
+            memo_h[1] = th;
+            const int32_t tl = memo_len[0], tc = memo_cls[0];
+            memo_len[0] = memo_len[1];
+            memo_cls[0] = memo_cls[1];
+            memo_len[1] = tl;
+            memo_cls[1] = tc;
+          }
+        } else {
+          uint32_t slot = 0;
+          const int role = shape_probe(c, h, &slot);
+          if (role == 1) {
+            cls = row_program_class(c, (int32_t)I, sm, w);
+            int32_t off = -1;
+            if (lane == 0) {
+              off = (int32_t)atomicAdd(&c.counters[5], slen);
+              if ((int64_t)off + slen > c.spool_cap) off = -1;
+            }
+            off = __shfl_sync(0xffffffffu, off, 0);
+            if (off >= 0)
+              for (int x = lane; x < slen; x += 32) c.spool[off + x] = sh[x];
+            __syncwarp();
+            if (lane == 0) {
+              c.soff[slot] = off;
+              c.scls[slot] = cls;
+              __threadfence();  // the shape, its offset and class before the flag
+              atomicExch(&c.sready[slot], 1);
+            }
+          } else if (role == 2) {
+            int ready = 0;
+            if (lane == 0) ready = atomicAdd(&c.sready[slot], 0);
+            ready = __shfl_sync(0xffffffffu, ready, 0);
+            __threadfence();
+            bool same = false;
+            int32_t k = -2;
+            if (ready) {
+              const int32_t off = __ldcg(&c.soff[slot]);
+              k = __ldcg(&c.scls[slot]);
+              if (off >= 0 && __ldcg(&c.spool[off]) == sh[0]) {
+                same = true;
+                for (int x = lane; x < slen; x += 32) same = same && __ldcg(&c.spool[off + x]) == sh[x];
+                same = __all_sync(0xffffffffu, same);
+              }
+            }
+            cls = (same && k != -3) ? k : row_program_class(c, (int32_t)I, sm, w);
+          } else {
+            cls = row_program_class(c, (int32_t)I, sm, w);
+          }
+          // remember this shape and its class (settled classes only)
+          if (cls >= 0 || cls == -2) {
+            const int old = memo[1];
+            memo[1] = memo[0];
+            memo_h[1] = memo_h[0];
+            memo_len[1] = memo_len[0];
+            memo_cls[1] = memo_cls[0];
+            memo[0] = buf;
+            memo_h[0] = h;
+            memo_len[0] = slen;
+            memo_cls[0] = cls;
+            buf = old;
           }
         }
-        cls = (same && k != -3) ? k : row_program_class(c, (int32_t)I, sm, w);
-      } else {
-        cls = row_program_class(c, (int32_t)I, sm, w);
       }
+      if (lane == 0) {
+        c.row_class[I] = cls;
+        if (cls == -2) atomicAdd(&c.counters[2], 1);
+        if (cls == -3) atomicAdd(&c.counters[4], 1);
+      }
+      __syncwarp();
     }
-    if (lane == 0) {
-      c.row_class[I] = cls;
-      if (cls == -2) atomicAdd(&c.counters[2], 1);
-      if (cls == -3) atomicAdd(&c.counters[4], 1);
-    }
-    __syncwarp();
   }
 }
 
