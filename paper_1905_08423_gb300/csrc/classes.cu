@@ -477,13 +477,14 @@ __global__ void __launch_bounds__(kSigWarps * 32) k_class_build(ClassArgs c) {
   int32_t memo_len[2] = {0, 0}, memo_cls[2] = {-2, -2};
   const int64_t warps = (int64_t)gridDim.x * kSigWarps;
   for (int64_t run = (int64_t)blockIdx.x * kSigWarps + w; run * 32 < c.n; run += warps) {
+    // one row outside the limits, or a full table, sends the whole plan to the
+    // general kernel: nothing left to learn, so every warp stops.  Checked once
+    // a run: every warp reading the same word each row would queue on it.
+    int stop = 0;
+    if (lane == 0) stop = ((volatile int32_t*)c.counters)[2] > 0 || ((volatile int32_t*)c.counters)[3] != 0;
+    if (__shfl_sync(0xffffffffu, stop, 0)) return;
     const int64_t I1 = min((int64_t)c.n, run * 32 + 32);
     for (int64_t I = run * 32; I < I1; ++I) {
-      // one row outside the limits, or a full table, sends the whole plan to the
-      // general kernel: nothing left to learn, so every warp stops
-      int stop = 0;
-      if (lane == 0) stop = ((volatile int32_t*)c.counters)[2] > 0 || ((volatile int32_t*)c.counters)[3] != 0;
-      if (__shfl_sync(0xffffffffu, stop, 0)) return;
       if (c.g.P.rp[I + 1] == c.g.P.rp[I]) {  // never visited
         if (lane == 0) c.row_class[I] = -1;
         continue;
