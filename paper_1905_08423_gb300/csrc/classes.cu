@@ -294,7 +294,7 @@ __device__ int compute_shape(const SigGeom& g, int32_t I, int32_t* sh) {
     pa = g.P.rp[k + 1] - pb;
   }
   if (__any_sync(0xffffffffu, pa > kFastMaxB)) return -1;
-  int32_t off = 1 + pa;  // inclusive scan of 1 + pa over the entries of A(I,:)
+  int32_t off = lane < na ? 1 + pa : 0;  // inclusive scan of 1 + pa over the entries of A(I,:)
 #pragma unroll
   for (int d = 1; d < 32; d <<= 1) {
     const int32_t y = __shfl_up_sync(0xffffffffu, off, d);
