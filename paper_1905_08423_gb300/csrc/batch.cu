@@ -131,12 +131,6 @@ int prepare_fast_side(ptap_batch* b, const std::vector<ptap_plan*>& fp, const st
     want_jit = want_jit || p->cfg.jit;
     max_classes = std::max(max_classes, p->cfg.jit ? p->cfg.jit_max_classes : 0);
   }
-  // the specialised code reads rows with aligned 16-byte loads
-  auto al = [](const void* q) { return ((uintptr_t)q & 15u) == 0; };
-  for (size_t i = 0; i < fp.size(); ++i) {
-    const int32_t q = fq[i];
-    if (!al(A[q].val) || !al(A[q].col_idx) || !al(P[q].val) || !al(plans[q]->aq)) want_jit = false;
-  }
   std::vector<int32_t*> slots;
   if (want_jit &&
       jit_prepare_batch(fp.data(), (int)fp.size(), max_classes, b->fast_threads, b->mem, s, &b->jit_fn, slots,
@@ -198,8 +192,6 @@ int prepare_fast_side(ptap_batch* b, const std::vector<ptap_plan*>& fp, const st
     f.row_loc = p->compact ? p->row_loc : nullptr;
     f.chunk_nnz = p->compact ? p->chunk_nnz : nullptr;
     f.loc_bits = p->loc_bits;
-    f.a_nnz = (int32_t)p->nnz_a;
-    f.p_nnz = (int32_t)p->nnz_p;
   }
   PTAP_TRY(b->mem.get(&b->d_desc_fast, hf.size() * sizeof(ptapk::FastArgs<V>)));
   PTAP_CUDA(cudaMemcpyAsync(b->d_desc_fast, hf.data(), hf.size() * sizeof(ptapk::FastArgs<V>),

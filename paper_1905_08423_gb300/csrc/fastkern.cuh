@@ -81,43 +81,7 @@ struct FastArgs {
   const int32_t* row_loc;
   const int32_t* chunk_nnz;
   int32_t loc_bits;
-  // entries of A and P (bounds of the 16-byte loads of load_run)
-  int32_t a_nnz, p_nnz;
 };
-
-// v[0, N) = p[e, e + N): N consecutive entries of an array of `end` entries,
-// read with aligned 16-byte loads of the window that covers them and the
-// misalignment selected out (no branch: each output is a chain of selects).
-// A lane's row then costs ceil((N + F - 1) / F) requests instead of N, each
-// inside one 32-byte sector; the rows of a warp's lanes lie apart, so this
-// cuts the sectors a warp's loads touch.  The base of p must be 16-byte
-// aligned (checked on the host).  Windows that would pass `end` read the
-// entries one by one.
-template <typename T, int N>
-__device__ __forceinline__ void load_run(const T* __restrict__ p, int32_t e, int32_t end, T (&v)[N]) {
-  constexpr int F = 16 / (int)sizeof(T);
-  constexpr int NW = (N + F - 1 + F - 1) / F * F;
-  const int32_t base = e & ~(F - 1);
-  const int shift = e - base;
-  if (base + NW <= end) {
-    T w[NW];
-#pragma unroll
-    for (int j = 0; j < NW / F; ++j) {
-      const uint4 q = __ldg(reinterpret_cast<const uint4*>(p + base) + j);
-      *reinterpret_cast<uint4*>(&w[j * F]) = q;
-    }
-#pragma unroll
-    for (int j = 0; j < N; ++j) {
-      T x = w[j];
-#pragma unroll
-      for (int s = 1; s < F; ++s) x = shift == s ? w[j + s] : x;
-      v[j] = x;
-    }
-  } else {
-#pragma unroll
-    for (int j = 0; j < N; ++j) v[j] = p[e + j];
-  }
-}
 
 // Adds v to *p, p in shared memory.  A relaxed reduction: the barrier that
 // ends the chunk orders it before the accumulator is read.

@@ -58,8 +58,6 @@ static FastArgs<V> fast_args(ptap_plan* p, const ptap_csr* A, const ptap_csr* P,
   a.row_loc = p->compact ? p->row_loc : nullptr;
   a.chunk_nnz = p->compact ? p->chunk_nnz : nullptr;
   a.loc_bits = p->loc_bits;
-  a.a_nnz = (int32_t)p->nnz_a;
-  a.p_nnz = (int32_t)p->nnz_p;
   return a;
 }
 
@@ -166,14 +164,10 @@ int prepare_fast(ptap_plan* p) {
   return PTAP_OK;
 }
 
-static bool aligned16(const void* q) { return ((uintptr_t)q & 15u) == 0; }
-
 template <typename V>
 static int launch_fast_t(ptap_plan* p, const ptap_csr* A, const ptap_csr* P, void* C, cudaStream_t s) {
   FastArgs<V> args = fast_args<V>(p, A, P, C);
-  // the specialised code reads rows with aligned 16-byte loads; arrays whose
-  // base is not 16-byte aligned run on the interpreter
-  if (p->jit_fn && aligned16(A->val) && aligned16(A->col_idx) && aligned16(P->val) && aligned16(p->aq)) {
+  if (p->jit_fn) {
     const int grid = (int)std::min<int64_t>(p->nchunks, (int64_t)num_sms() * p->jit_per_sm);
     if (grid <= 0) return PTAP_OK;
     args.rs_global = (V*)p->jit_rs;

@@ -192,23 +192,21 @@ std::string gen_class(int cls, const uint8_t* g, bool cached, int loc_bits) {
           " int32_t i1, V* acc, const int32_t* roff, int32_t I) {\n",
           cls);
   o += "  const int lane = threadIdx.x & 31;\n  const bool valid = f + lane < f1;\n"
-       "  const int32_t ra = a.A.rp[I];\n  const V* Pv = a.P.val;\n";
-  // the lane's row of A, and the P rows it combines, as aligned 16-byte windows
-  appendf(o, "  V av[%d];\n  load_run<V, %d>(a.A.val, ra, a.a_nnz, av);\n  int32_t qv[%d];\n", na, na, na);
-  if (cached) {
-    appendf(o, "  load_run<int32_t, %d>(a.aq, ra, a.a_nnz, qv);\n", na);
-  } else {
-    appendf(o, "  {\n    int32_t kc[%d];\n    load_run<int32_t, %d>(a.A.ci, ra, a.a_nnz, kc);\n", na, na);
-    appendf(o, "#pragma unroll\n    for (int x = 0; x < %d; ++x) qv[x] = a.P.rp[kc[x]];\n  }\n", na);
+       "  const int32_t ra = a.A.rp[I];\n"
+       "  const int32_t* Aci = a.A.ci + ra;\n  const V* Av = a.A.val + ra;\n  const V* Pv = a.P.val;\n";
+  if (cached) o += "  const int32_t* Aq = a.aq + ra;\n  (void)Aci;\n";
+  for (int x = 0; x < na; ++x) {
+    if (cached)
+      appendf(o, "  const V a%d = Av[%d];\n  const int32_t q%d = Aq[%d];\n", x, x, x, x);
+    else
+      appendf(o, "  const V a%d = Av[%d];\n  const int32_t q%d = a.P.rp[Aci[%d]];\n", x, x, x, x);
   }
-  for (int x = 0; x < na; ++x)
-    if (pa[x] > 0) appendf(o, "  V p%d[%d];\n  load_run<V, %d>(Pv, qv[%d], a.p_nnz, p%d);\n", x, pa[x], pa[x], x, x);
   // slots of the row of A P, products summed in the interpreter's (a, b) order
   for (int t = 0; t < r; ++t) {
     appendf(o, "  V R%d = V(0);\n", t);
     for (int x = 0; x < na; ++x)
       for (int b = 0; b < pa[x]; ++b)
-        if (tsec[x * 8 + b] == t) appendf(o, "  R%d += av[%d] * p%d[%d];\n", t, x, x, b);
+        if (tsec[x * 8 + b] == t) appendf(o, "  R%d += a%d * Pv[q%d + %d];\n", t, x, x, b);
   }
   // outer product: the next entry of P(I,:) is loaded while this one is added
   o += "  const int32_t rp = a.P.rp[I];\n";
