@@ -256,12 +256,13 @@ struct ClassArgs {
   int32_t* spool;
   int32_t* soff;             // pool offset of each slot's shape
   int64_t spool_cap;
+  const int32_t* crep;       // representative of each C row (k_crow_rep), -1 for rows over 255
 };
 
 constexpr int kSigWarps = 4;
 constexpr uint32_t kMaxProbes = 256;  // linear probes of the class table before it counts as full
 
-constexpr int kShapeCap = 512;       // words of a row's shape kept on chip; longer rows skip the shape table
+constexpr int kShapeCap = 320;       // words of a row's shape kept on chip; longer rows skip the shape table
 
 struct SigSmem {
   __align__(16) uint8_t sig[kSigWarps][kFastSigCap];
@@ -273,15 +274,15 @@ struct SigSmem {
 // The shape of fine row I: everything its program depends on, relative to
 // c = the first column of P(I,:):
 //   na, pI, (P.ci of P(I,:)) - c, then per entry a of A(I,:): pa, (columns of
-//   P(k_a,:)) - c, then per entry s of P(I,:): L = length of C row i_s and
-//   (its columns) - c.
+//   P(k_a,:)) - c, then per entry s of P(I,:): the representative of C row
+//   i_s (k_crow_rep: equal representatives, equal columns relative to i_s).
 // Two rows with equal shapes have equal programs: the slots of A P follow
 // from the order of the relative columns, the positions in C from the
 // relative C rows.  Returns the length in words; -1 if the row is outside
 // the fast-path limits (as compute_sig would find, except the row of A P
 // being too long, which its program reveals); -4 if the shape exceeds the
 // on-chip buffer.
-__device__ int compute_shape(const SigGeom& g, int32_t I, int32_t* sh) {
+__device__ int compute_shape(const SigGeom& g, const int32_t* __restrict__ crep, int32_t I, int32_t* sh) {
   const int lane = threadIdx.x & 31;
   const int32_t a0 = g.A.rp[I], na = g.A.rp[I + 1] - a0;
   const int32_t p0 = g.P.rp[I], pI = g.P.rp[I + 1] - p0;
@@ -313,15 +314,15 @@ __device__ int compute_shape(const SigGeom& g, int32_t I, int32_t* sh) {
     sh[o] = pa;
     for (int32_t b = 0; b < pa; ++b) sh[o + 1 + b] = g.P.ci[pb + b] - base;
   }
-  for (int32_t s = 0; s < pI; ++s) {
-    const int32_t i = g.P.ci[p0 + s];
-    const int32_t c0 = g.C.rp[i], L = g.C.rp[i + 1] - c0;  // the same in every lane
-    if (L > 255) return -1;
-    if (len + 1 + L > kShapeCap) return -4;
-    if (lane == 0) sh[len] = L;
-    for (int32_t j = lane; j < L; j += 32) sh[len + 1 + j] = g.C.ci[c0 + j] - base;
-    len += 1 + L;
-  }
+  // the C rows of P(I,:): their representatives (rows with equal columns
+  // relative to their own index share one, see k_crow_rep); with the
+  // section of P(I,:) above, which fixes each i_s - c, this fixes the C rows
+  // relative to c
+  int32_t rep = 0;
+  if (lane < pI) rep = crep[g.P.ci[p0 + lane]];
+  if (__any_sync(0xffffffffu, lane < pI && rep < 0)) return -1;  // a C row too long for a program
+  if (lane < pI) sh[len + lane] = rep;
+  len += pI;
   __syncwarp();
   return len;
 }
@@ -429,6 +430,105 @@ __device__ int32_t row_program_class(const ClassArgs& c, int32_t I, SigSmem& sm,
   return len < 0 ? -2 : program_class(c, sm.sig[w], len);
 }
 
+// Representatives of the rows of C: rep[i] = the first row met, in this
+// launch, whose columns relative to its own index equal row i's (C(i,:) - i);
+// -1 for a row longer than 255 (outside the class programs).  Equal
+// representatives mean equal relative rows, which is all the fine rows'
+// programs need of C.  A table keyed by a hash of the relative row holds the
+// published representatives; a row compares itself with the representative's
+// row (in C itself) before taking it, so a collision only costs a row its
+// own representative.  Warps take runs of 32 consecutive rows and remember
+// their last two representatives on chip.  No warp waits on another.
+struct CrowArgs {
+  CsrI C;
+  unsigned long long* key;
+  int32_t* ready;
+  int32_t* rep_of_slot;
+  int tlog2;
+  int32_t* rep;
+};
+
+__device__ bool same_crow(const CsrI& C, int32_t i, int32_t r) {
+  const int lane = threadIdx.x & 31;
+  const int32_t ci0 = C.rp[i], L = C.rp[i + 1] - ci0, cr0 = C.rp[r];
+  if (C.rp[r + 1] - cr0 != L) return false;  // the same in every lane
+  bool same = true;
+  for (int32_t j = lane; j < L; j += 32) same = same && (C.ci[ci0 + j] - i == C.ci[cr0 + j] - r);
+  return __all_sync(0xffffffffu, same);
+}
+
+__global__ void __launch_bounds__(128) k_crow_rep(CrowArgs a) {
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t mask = (1u << a.tlog2) - 1u;
+  int32_t memo[2] = {-1, -1};
+  unsigned long long memo_h[2] = {kEmptyKey, kEmptyKey};
+  const int64_t warps = (int64_t)gridDim.x * 4;
+  for (int64_t run = (int64_t)blockIdx.x * 4 + w; run * 32 < a.C.nrows; run += warps) {
+    const int64_t i1 = min((int64_t)a.C.nrows, run * 32 + 32);
+    for (int64_t i = run * 32; i < i1; ++i) {
+      const int32_t c0 = a.C.rp[i], L = a.C.rp[i + 1] - c0;
+      if (L > 255) {
+        if (lane == 0) a.rep[i] = -1;
+        continue;
+      }
+      // hash of the relative row
+      unsigned long long h = 0x9ae16a3b2f90404full ^ mix64((unsigned long long)(lane + 1) * 0x9e3779b97f4a7c15ull);
+      for (int32_t j = lane; j < L; j += 32)
+        h = (h ^ (unsigned long long)(uint32_t)(a.C.ci[c0 + j] - (int32_t)i)) * 0x100000001b3ull;
+      h = mix64(h + (unsigned long long)lane * 0x632be59bd9b4e019ull + (unsigned long long)L);
+#pragma unroll
+      for (int d = 16; d > 0; d >>= 1) h ^= __shfl_xor_sync(0xffffffffu, h, d);
+      if (h == kEmptyKey) h = 0;
+      int32_t r = -1;
+      for (int q = 0; q < 2 && r < 0; ++q)
+        if (memo_h[q] == h && memo[q] >= 0 && same_crow(a.C, (int32_t)i, memo[q])) r = memo[q];
+      if (r < 0) {
+        uint32_t slot = (uint32_t)(h >> 24) & mask;
+        int role = 0;
+        if (lane == 0) {
+          for (uint32_t probe = 0; probe <= mask && probe < kMaxProbes; ++probe) {
+            unsigned long long old = *(volatile unsigned long long*)&a.key[slot];
+            if (old == kEmptyKey) old = atomicCAS(&a.key[slot], kEmptyKey, h);
+            if (old == kEmptyKey) {
+              role = 1;
+              break;
+            }
+            if (old == h) {
+              role = 2;
+              break;
+            }
+            slot = (slot + 1) & mask;
+          }
+        }
+        role = __shfl_sync(0xffffffffu, role, 0);
+        slot = __shfl_sync(0xffffffffu, slot, 0);
+        if (role == 1) {
+          r = (int32_t)i;
+          if (lane == 0) {
+            a.rep_of_slot[slot] = r;
+            __threadfence();
+            atomicExch(&a.ready[slot], 1);
+          }
+        } else if (role == 2) {
+          int rdy = 0;
+          if (lane == 0) rdy = atomicAdd(&a.ready[slot], 0);
+          rdy = __shfl_sync(0xffffffffu, rdy, 0);
+          __threadfence();
+          const int32_t cand = rdy ? __ldcg(&a.rep_of_slot[slot]) : -1;
+          r = (cand >= 0 && same_crow(a.C, (int32_t)i, cand)) ? cand : (int32_t)i;
+        } else {
+          r = (int32_t)i;  // table full: the row is its own representative
+        }
+        memo[1] = memo[0];
+        memo_h[1] = memo_h[0];
+        memo[0] = r;
+        memo_h[0] = h;
+      }
+      if (lane == 0) a.rep[i] = r;
+    }
+  }
+}
+
 // Probes the shape table for the key h: 1 = this row inserted it, 2 = it
 // exists, 0 = no room (the row takes the full path).  *slot gets the slot.
 __device__ int shape_probe(const ClassArgs& c, unsigned long long h, uint32_t* slot_out) {
@@ -490,7 +590,7 @@ __global__ void __launch_bounds__(kSigWarps * 32) k_class_build(ClassArgs c) {
         continue;
       }
       int32_t* sh = sm.shape[w][buf];
-      const int slen = compute_shape(c.g, (int32_t)I, sh);
+      const int slen = compute_shape(c.g, c.crep, (int32_t)I, sh);
       int32_t cls = -2;
       if (slen == -1) {
         cls = -2;  // outside the limits
@@ -769,6 +869,20 @@ int build_classes(ptap_plan* p, const ptap_csr* A, const ptap_csr* P, cudaStream
   PTAP_TRY(sc.get(&row_class, p->n));
   PTAP_TRY(sc.get(&class_off, tcap + 1));
   PTAP_TRY(sc.get(&pool, pool_cap));
+  // representatives of C's rows (k_crow_rep), which the fine rows' shapes name
+  int32_t *crep = nullptr, *cready = nullptr, *crslot = nullptr;
+  unsigned long long* ckey = nullptr;
+  PTAP_TRY(sc.get(&crep, std::max(p->m, 1)));
+  PTAP_TRY(sc.get(&ckey, tcap));
+  PTAP_TRY(sc.get(&cready, tcap));
+  PTAP_TRY(sc.get(&crslot, tcap));
+  PTAP_CUDA(cudaMemsetAsync(ckey, 0xff, tcap * sizeof(unsigned long long), s));
+  PTAP_CUDA(cudaMemsetAsync(cready, 0, tcap * sizeof(int32_t), s));
+  {
+    CrowArgs ca{CsrI{p->m, p->m, p->c_rp, p->c_ci}, ckey, cready, crslot, tlog2, crep};
+    k_crow_rep<<<num_sms() * 16, 128, 0, s>>>(ca);
+    PTAP_LAUNCHED();
+  }
   // the shape table in front of the program table (k_class_build)
   const int64_t spool_cap = (int64_t)1 << 22;
   unsigned long long* skey = nullptr;
@@ -803,6 +917,7 @@ int build_classes(ptap_plan* p, const ptap_csr* A, const ptap_csr* P, cudaStream
   c.spool = spool;
   c.soff = soff;
   c.spool_cap = spool_cap;
+  c.crep = crep;
   // latency-bound warp-per-row work: fill the SMs (16 CTAs of 4 warps each)
   const int grid = num_sms() * 16;
   PhaseRange r_build("ptap: class signatures", s);
