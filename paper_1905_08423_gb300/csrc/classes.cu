@@ -257,6 +257,8 @@ struct ClassArgs {
   int32_t* soff;             // pool offset of each slot's shape
   int64_t spool_cap;
   const int32_t* crep;       // representative of each C row (k_crow_rep), -1 for rows over 255
+  int32_t* vlist;            // the rows marked -3, in the order they were met (first vcap of them)
+  int32_t vcap;
 };
 
 constexpr int kSigWarps = 4;
@@ -679,18 +681,25 @@ __global__ void __launch_bounds__(kSigWarps * 32) k_class_build(ClassArgs c) {
       if (lane == 0) {
         c.row_class[I] = cls;
         if (cls == -2) atomicAdd(&c.counters[2], 1);
-        if (cls == -3) atomicAdd(&c.counters[4], 1);
+        if (cls == -3) {
+          const int32_t k = atomicAdd(&c.counters[4], 1);
+          if (k < c.vcap) c.vlist[k] = (int32_t)I;
+        }
       }
       __syncwarp();
     }
   }
 }
 
-__global__ void __launch_bounds__(kSigWarps * 32) k_class_verify(ClassArgs c) {
+// nlist >= 0: the rows to settle are vlist[0, nlist); otherwise every row
+// marked -3 (the list overflowed).
+__global__ void __launch_bounds__(kSigWarps * 32) k_class_verify(ClassArgs c, int32_t nlist) {
   __shared__ SigSmem sm;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t mask = (1u << c.tlog2) - 1u;
-  for (int64_t I = (int64_t)blockIdx.x * kSigWarps + w; I < c.n; I += (int64_t)gridDim.x * kSigWarps) {
+  const int64_t total = nlist >= 0 ? nlist : c.n;
+  for (int64_t x = (int64_t)blockIdx.x * kSigWarps + w; x < total; x += (int64_t)gridDim.x * kSigWarps) {
+    const int64_t I = nlist >= 0 ? c.vlist[x] : x;
     if (c.row_class[I] != -3) continue;
     const int len = compute_sig(c.g, (int32_t)I, sm.sig[w], sm.cand[w], sm.keys[w], c.status);
     int32_t cls = -2;
@@ -918,6 +927,8 @@ int build_classes(ptap_plan* p, const ptap_csr* A, const ptap_csr* P, cudaStream
   c.soff = soff;
   c.spool_cap = spool_cap;
   c.crep = crep;
+  c.vcap = 1 << 20;
+  PTAP_TRY(sc.get(&c.vlist, c.vcap));
   // latency-bound warp-per-row work: fill the SMs (16 CTAs of 4 warps each)
   const int grid = num_sms() * 16;
   PhaseRange r_build("ptap: class signatures", s);
@@ -928,7 +939,9 @@ int build_classes(ptap_plan* p, const ptap_csr* A, const ptap_csr* P, cudaStream
   PTAP_CUDA(cudaStreamSynchronize(s));
   if (h[2] > 0 || h[3]) return PTAP_OK;  // some row outside the limits, or table full
   if (h[4] > 0) {  // rows that met their key before its program was published
-    k_class_verify<<<grid, kSigWarps * 32, 0, s>>>(c);
+    const int32_t nlist = h[4] <= c.vcap ? h[4] : -1;
+    k_class_verify<<<nlist >= 0 ? (int)std::max<int64_t>(1, std::min<int64_t>(grid, ceil_div(nlist, kSigWarps))) : grid,
+                     kSigWarps * 32, 0, s>>>(c, nlist);
     PTAP_LAUNCHED();
     PTAP_CUDA(cudaMemcpyAsync(h, counters, sizeof(h), cudaMemcpyDeviceToHost, s));
     PTAP_CUDA(cudaStreamSynchronize(s));
