@@ -47,7 +47,7 @@ def candidate_list(fast_path: bool, n_classes: int, value_bytes: int, smem_optin
     plans: CTAs of 512 and 1024 threads, each with the largest chunk the
     accumulator allows and smaller ones (fewer entries per CTA: more CTAs for
     the same C, more fine rows visiting two chunks), with and without the
-    cached P row start per entry of A at the largest chunk, and plan-time
+    cached P row start per entry of A, and plan-time
     specialisation of the most visited 16 or 32 classes (fewer if the problem
     has fewer), plus the interpreter alone.  For plans outside the class
     programs: the sort-based and the hash-group general kernels over lanes per
@@ -60,11 +60,13 @@ def candidate_list(fast_path: bool, n_classes: int, value_bytes: int, smem_optin
         spec = sorted({min(16, n_classes), min(32, n_classes)} - {0})
         mid = 32768 if lim > 32768 else max(1024, (lim * 5 // 6) & ~4095)
         for bt in (1024, 512):
-            for ch in sorted({lim, mid, max(1024, lim // 2)}, reverse=True):
+            chunks = sorted({lim, mid, max(1024, lim // 2)}, reverse=True)
+            for ch in chunks:
                 for k in spec:
                     out.append(dict(specialize=k, block_threads=bt, chunk_entries=ch))
-            # the plan's cached index (Section 4.2's memory-for-time trade) at the largest chunk
-            out.append(dict(specialize=spec[-1], block_threads=bt, chunk_entries=lim, cache_indices=True))
+            # the plan's cached index (Section 4.2's memory-for-time trade), every chunk size
+            for ch in chunks:
+                out.append(dict(specialize=spec[-1], block_threads=bt, chunk_entries=ch, cache_indices=True))
         out.append(dict())                                    # interpreter, 256 threads
         out.append(dict(block_threads=1024, chunk_entries=lim))  # interpreter, large CTAs
     out.append(dict(class_programs=False))                   # sort-based general kernel
