@@ -801,6 +801,62 @@ __global__ void k_visit_keys(const int32_t* __restrict__ fptr, const int32_t* __
   }
 }
 
+// Class-major visit order without a comparison sort: a warp per chunk counts
+// its visits per class (a histogram of K counters in shared memory), scans the
+// counts, and places the visits batch by batch in their input order -- lanes
+// of one class take consecutive slots by rank among their peers -- so each
+// class keeps the ascending order the lists come in.  The keys it writes are
+// those k_visit_keys forms (class above the position bits), in sorted order:
+// the same result as the segmented sort of those keys, when one block covers
+// the chunk (visit_block_log2 = 0).
+__global__ void k_visit_class_sort(const int32_t* __restrict__ fptr, const int32_t* __restrict__ frows,
+                                   int32_t nch, const int32_t* __restrict__ row_class, int32_t K,
+                                   int kBlockBits, bool rank, int32_t* __restrict__ keys_out,
+                                   int32_t* __restrict__ frows_out) {
+  extern __shared__ int32_t hsm[];
+  const int lane = threadIdx.x & 31;
+  int32_t* hist = hsm + (threadIdx.x >> 5) * K;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int32_t dmask = (1 << kBlockBits) - 1;
+  for (int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < nch; c += nw) {
+    const int32_t f0 = fptr[c], f1 = fptr[c + 1];
+    if (f0 == f1) continue;
+    for (int32_t k = lane; k < K; k += 32) hist[k] = 0;
+    __syncwarp();
+    for (int32_t f = f0 + lane; f < f1; f += 32) atomicAdd(&hist[row_class[frows[f]]], 1);
+    __syncwarp();
+    int32_t carry = f0;  // output positions are absolute
+    for (int32_t b = 0; b < K; b += 32) {
+      const int32_t v = b + lane < K ? hist[b + lane] : 0;
+      int32_t incl = v;
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const int32_t y = __shfl_up_sync(0xffffffffu, incl, d);
+        if (lane >= d) incl += y;
+      }
+      if (b + lane < K) hist[b + lane] = carry + incl - v;
+      carry += __shfl_sync(0xffffffffu, incl, 31);
+    }
+    __syncwarp();
+    const int32_t basef = frows[f0];
+    for (int32_t f = f0; f < f1; f += 32) {
+      const bool ok = f + lane < f1;
+      const int32_t I = ok ? frows[f + lane] : 0;
+      const int32_t cl = ok ? row_class[I] : -1;
+      const unsigned peers = __match_any_sync(0xffffffffu, cl);
+      const int32_t pos = ok ? hist[cl] + __popc(peers & ((1u << lane) - 1u)) : 0;
+      __syncwarp();
+      if (ok) {
+        const int32_t d = rank ? (f + lane - f0) : (I - basef);
+        frows_out[pos] = I;
+        keys_out[pos] = (cl << kBlockBits) | (d & dmask);
+        if ((peers >> lane) == 1u) hist[cl] += __popc(peers);  // the group's last lane moves the cursor
+      }
+      __syncwarp();
+    }
+  }
+}
+
 __global__ void k_seg_flags(const int32_t* __restrict__ fptr, int32_t nch, const int32_t* __restrict__ keys,
                             int shift, int kBlockBits, int32_t* flag) {
   const int lane = threadIdx.x & 31;
@@ -1026,12 +1082,27 @@ int build_classes(ptap_plan* p, const ptap_csr* A, const ptap_csr* P, cudaStream
   PTAP_TRY(sc.get(&keys, p->nfrows));
   PTAP_TRY(sc.get(&flag, p->nfrows));
   PTAP_TRY(sc.get(&segid, p->nfrows + 1));
-  k_visit_keys<<<grid, 256, 0, s>>>(p->chunk_fptr, p->chunk_frows, p->nchunks, row_class, shift,
-                                    kBlockBits, rank, keys);
-  PTAP_LAUNCHED();
   {
     PhaseRange r_sort("ptap: visit order sort", s);
-    PTAP_TRY(segmented_sort(p->mem, p->chunk_fptr, p->nchunks, keys, p->chunk_frows, -1, s));
+    constexpr int32_t kCountSortMaxClasses = 2048;
+    if (p->cfg.visit_block_log2 <= 0 && K <= kCountSortMaxClasses) {
+      // class-major order by counting (k_visit_class_sort) into a new visit list
+      int32_t* sorted = nullptr;
+      PTAP_TRY(p->mem.get_n(&sorted, std::max<int64_t>(p->nfrows, 1)));
+      const int warps = 4;
+      const size_t smem = (size_t)warps * K * sizeof(int32_t);
+      PTAP_TRY(grow_smem_limit((const void*)k_visit_class_sort, (int)smem));
+      k_visit_class_sort<<<grid, warps * 32, smem, s>>>(p->chunk_fptr, p->chunk_frows, p->nchunks, row_class, K,
+                                                        kBlockBits, rank, keys, sorted);
+      PTAP_LAUNCHED();
+      p->mem.put(p->chunk_frows);
+      p->chunk_frows = sorted;
+    } else {
+      k_visit_keys<<<grid, 256, 0, s>>>(p->chunk_fptr, p->chunk_frows, p->nchunks, row_class, shift,
+                                        kBlockBits, rank, keys);
+      PTAP_LAUNCHED();
+      PTAP_TRY(segmented_sort(p->mem, p->chunk_fptr, p->nchunks, keys, p->chunk_frows, -1, s));
+    }
   }
   k_seg_flags<<<grid, 256, 0, s>>>(p->chunk_fptr, p->nchunks, keys, shift, kBlockBits, flag);
   PTAP_LAUNCHED();
