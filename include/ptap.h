@@ -127,7 +127,12 @@ typedef struct {
                                at symbolic time (default); 1 = the plan compiles nothing, and a
                                batch that includes it (ptap_batch_create) compiles one kernel for
                                the most visited classes over all its plans */
-  int32_t reserved[2];
+  int32_t specialize_async; /* with specialize = k > 0 and scope 0: nonzero compiles the plan's
+                               code in a background thread, so ptap_symbolic returns without
+                               waiting for NVRTC; numeric calls run the interpreter until the
+                               compiled kernel is loaded, then switch to it (ptap_stats'
+                               n_specialized stays 0 until then).  0: compile at symbolic time */
+  int32_t reserved[1];
 } ptap_config;
 
 /* Statistics of a plan (host struct filled by ptap_plan_stats).  The byte

@@ -45,6 +45,7 @@ Config resolve_config(const ptap_config* c) {
   r.jit = c->specialize > 0 ? 1 : 0;
   if (c->specialize > 0) r.jit_max_classes = std::min(c->specialize, 256);
   r.jit_scope = c->specialize_scope == 1 ? 1 : 0;
+  r.jit_async = c->specialize_async != 0 ? 1 : 0;
   const int bt = pick(c->block_threads, r.block_threads);
   r.block_threads = (bt == 64 || bt == 128 || bt == 256 || bt == 512 || bt == 1024) ? bt : r.block_threads;
   const int g = pick(c->group_lanes, r.group_lanes);
@@ -97,8 +98,9 @@ int ptap_plan_stats(const ptap_plan* p, ptap_stats* o) {
   o->n_classes = p->nclasses;
   o->n_segments = p->nseg;
   o->n_pieces = (int32_t)std::min<int64_t>(p->npieces, INT32_MAX);
-  o->n_specialized = p->jit_fn ? p->jit_classes : 0;
-  o->specialized_permille = p->jit_fn ? (int32_t)(p->jit_coverage * 1000.0 + 0.5) : 0;
+  const bool jit = p->jit_fn.load(std::memory_order_acquire) != nullptr;
+  o->n_specialized = jit ? p->jit_classes : 0;
+  o->specialized_permille = jit ? (int32_t)(p->jit_coverage * 1000.0 + 0.5) : 0;
   o->specialize_us = (int32_t)std::min(p->jit_ms * 1000.0, 2.0e9);
   o->compact_chunks = p->compact ? 1 : 0;
   return PTAP_OK;
@@ -116,6 +118,11 @@ int ptap_plan_check(ptap_plan* p, void* stream) {
 
 void ptap_plan_destroy(ptap_plan* p) {
   if (!p) return;
+  if (p->jit_thread) {  // a background compile finishes before the plan goes
+    p->jit_thread->join();
+    delete p->jit_thread;
+    p->jit_thread = nullptr;
+  }
   cudaStreamSynchronize(p->stream);
   ptap::host_stage_free(p);
   p->mem.release_all();

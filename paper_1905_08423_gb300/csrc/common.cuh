@@ -8,7 +8,9 @@
 
 #include <algorithm>
 #include <chrono>
+#include <atomic>
 #include <cstdio>
+#include <thread>
 #include <cstring>
 #include <unordered_map>
 #include <vector>
@@ -171,6 +173,7 @@ struct Config {
   int jit = 0;                // specialise the most frequent classes with NVRTC
   int jit_max_classes = 8;
   int jit_scope = 0;          // 0: the plan's own kernel; 1: only batches compile code
+  int jit_async = 0;          // compile the plan's kernel in a background thread
   int block_threads = 256;
   int group_lanes = 8;
   int ap_slots = 64;
@@ -256,7 +259,11 @@ struct ptap_plan {
   int32_t* chunk_piece = nullptr; // [nchunks+1] first piece of each chunk
 
   // plan-time specialised kernel (jit.cu); null when the interpreter runs
-  void* jit_fn = nullptr;
+  // set (release) once the specialised code is loaded: at symbolic time, or
+  // by jit_thread when the compile runs in the background (specialize_async);
+  // launches read it (acquire) and run the interpreter until then
+  std::atomic<void*> jit_fn{nullptr};
+  std::thread* jit_thread = nullptr;
   void* jit_rs = nullptr;  // global scratch for the interpreted classes' rows of A P
   int32_t* jit_slot = nullptr;  // [nclasses] compiled-code number of each class, or -1
   int32_t* aq = nullptr;        // [nnz(A)] P.rp[A.ci[e]] when indices are cached

@@ -150,7 +150,7 @@ int build_index_cache(ptap_plan* p, const ptap_csr* A, const ptap_csr* P, cudaSt
 }
 
 int jit_prepare(ptap_plan* p);  // jit.cu
-int jit_launch(ptap_plan* p, const void* args, int grid, cudaStream_t s);
+int jit_launch(ptap_plan* p, void* fn, const void* args, int grid, cudaStream_t s);
 
 int prepare_fast(ptap_plan* p) {
   PTAP_TRY(p->dtype == PTAP_F64 ? prepare_fast_t<double>(p) : prepare_fast_t<float>(p));
@@ -167,11 +167,11 @@ int prepare_fast(ptap_plan* p) {
 template <typename V>
 static int launch_fast_t(ptap_plan* p, const ptap_csr* A, const ptap_csr* P, void* C, cudaStream_t s) {
   FastArgs<V> args = fast_args<V>(p, A, P, C);
-  if (p->jit_fn) {
+  if (void* fn = p->jit_fn.load(std::memory_order_acquire)) {
     const int grid = (int)std::min<int64_t>(p->nchunks, (int64_t)num_sms() * p->jit_per_sm);
     if (grid <= 0) return PTAP_OK;
     args.rs_global = (V*)p->jit_rs;
-    return jit_launch(p, &args, grid, s);
+    return jit_launch(p, fn, &args, grid, s);
   }
   const int grid = (int)std::min<int64_t>(p->nchunks, (int64_t)num_sms() * p->num_per_sm);
   if (grid <= 0) return PTAP_OK;

@@ -31,6 +31,8 @@
 #include <chrono>
 #include <map>
 #include <mutex>
+#include <new>
+#include <thread>
 #include <string>
 #include <vector>
 
@@ -383,14 +385,44 @@ int set_smem_and_occupancy(CUfunction fn, int threads, size_t smem, int* per_sm)
 
 }  // namespace
 
-// Picks the classes with the most visited rows, generates and compiles the
-// specialised kernel.  Returns PTAP_OK with p->jit_fn set, or any error (the
-// caller then keeps the interpreter).
+// Compiles `src` and publishes the kernel to the plan: its shared-memory
+// limit and occupancy first, then jit_fn (release), which launches read.
+// Runs on the caller's thread, or on p->jit_thread (background compile); it
+// touches no library allocator.  On failure jit_fn stays null and the
+// interpreter keeps serving the plan.
+static void jit_compile_publish(ptap_plan* p, std::string src, int dev,
+                                std::chrono::steady_clock::time_point t0) {
+  CUfunction fn = nullptr;
+  int per_sm = 0;
+  {
+    std::lock_guard<std::mutex> lock(g_mu);
+    if (cudaSetDevice(dev) != cudaSuccess) {
+      cudaGetLastError();
+      return;
+    }
+    if (compile_or_load(src, "ptap_jit_numeric", &fn) != PTAP_OK) return;
+    // The compiled classes keep their rows of A P in registers, so the
+    // interpreted ones use a global scratch instead of shared memory: the
+    // accumulator alone sets the shared-memory footprint.
+    if (set_smem_and_occupancy(fn, p->cfg.block_threads, p->jit_smem, &per_sm) != PTAP_OK) return;
+  }
+  p->jit_per_sm = std::min(per_sm, p->jit_per_sm);  // jit_per_sm holds the bound the scratch was sized for
+  p->jit_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  p->jit_fn.store((void*)fn, std::memory_order_release);
+}
+
+// Picks the classes with the most visited rows and generates the specialised
+// kernel, then compiles and loads it -- at once, or, with specialize_async, in
+// a background thread while numeric calls run the interpreter.  Returns
+// PTAP_OK, or any error (the caller then keeps the interpreter).
 int jit_prepare(ptap_plan* p) {
-  std::lock_guard<std::mutex> lock(g_mu);
-  load_apis();
+  {
+    std::lock_guard<std::mutex> lock(g_mu);
+    load_apis();
+  }
   if (!g_rtc.ok || !g_drv.ok || !p->fast || p->nclasses <= 0) return PTAP_ERR_UNSUPPORTED;
   cudaStream_t s = p->stream;
+  const auto t0 = std::chrono::steady_clock::now();
   ClassTable t;
   PTAP_TRY(read_classes(p, t));
   // Class ids come from a concurrent deduplication and differ between runs;
@@ -414,19 +446,16 @@ int jit_prepare(ptap_plan* p) {
   std::sort(hot.begin(), hot.end(), [&](int x, int y) { return t.bytes(x) < t.bytes(y); });
   std::vector<std::string> progs;
   for (int k : hot) progs.push_back(t.bytes(k));
-  const auto t0 = std::chrono::steady_clock::now();
-  const std::string src = build_source(p->dtype, progs, p->aq != nullptr, p->compact ? p->loc_bits : 0,
-                                       p->cfg.block_threads, 0);
-  CUfunction fn = nullptr;
-  PTAP_TRY(compile_or_load(src, "ptap_jit_numeric", &fn));
-  // The compiled classes keep their rows of A P in registers, so the
-  // interpreted ones use a global scratch instead of shared memory: the
-  // accumulator alone sets the shared-memory footprint.
-  const size_t smem = fast_smem_for(p, false);
-  int per_sm = 0;
-  PTAP_TRY(set_smem_and_occupancy(fn, p->cfg.block_threads, smem, &per_sm));
+  std::string src = build_source(p->dtype, progs, p->aq != nullptr, p->compact ? p->loc_bits : 0,
+                                 p->cfg.block_threads, 0);
+  // Resources the launch needs, sized before the compile (on this thread:
+  // the allocator is not shared with the background thread).  The scratch
+  // takes the resident-CTA bound that the thread count allows.
+  p->jit_smem = fast_smem_for(p, false);
+  const int bound_per_sm = std::max(1, 2048 / p->cfg.block_threads);
+  p->jit_per_sm = bound_per_sm;
   const size_t vb = p->dtype == PTAP_F64 ? 8 : 4;
-  const int64_t ctas = std::min<int64_t>(p->nchunks, (int64_t)num_sms() * per_sm);
+  const int64_t ctas = std::min<int64_t>(p->nchunks, (int64_t)num_sms() * bound_per_sm);
   void* rs = nullptr;
   PTAP_TRY(p->mem.get(&rs, (size_t)std::max<int64_t>(ctas, 1) * p->cfg.block_threads *
                                std::max(p->class_maxr, 1) * vb));
@@ -438,19 +467,23 @@ int jit_prepare(ptap_plan* p) {
   PTAP_CUDA(cudaStreamSynchronize(s));
   p->jit_slot = dslot;
   p->jit_rs = rs;
-  p->jit_smem = smem;
-  p->jit_fn = (void*)fn;
-  p->jit_per_sm = per_sm;
   p->jit_classes = (int)hot.size();
   p->jit_coverage = t.total ? (double)covered / (double)t.total : 0.0;
-  p->jit_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
-  return PTAP_OK;
+  int dev = 0;
+  PTAP_CUDA(cudaGetDevice(&dev));
+  if (p->cfg.jit_async) {
+    p->jit_thread = new (std::nothrow) std::thread(jit_compile_publish, p, std::move(src), dev, t0);
+    if (!p->jit_thread) jit_compile_publish(p, std::move(src), dev, t0);
+    return PTAP_OK;
+  }
+  jit_compile_publish(p, std::move(src), dev, t0);
+  return p->jit_fn.load(std::memory_order_acquire) ? PTAP_OK : PTAP_ERR_CUDA;
 }
 
-int jit_launch(ptap_plan* p, const void* args, int grid, cudaStream_t s) {
+int jit_launch(ptap_plan* p, void* fn, const void* args, int grid, cudaStream_t s) {
   void* params[1] = {const_cast<void*>(args)};
-  if (g_drv.launch((CUfunction)p->jit_fn, grid, 1, 1, p->cfg.block_threads, 1, 1, (unsigned)p->jit_smem,
-                   (CUstream)s, params, nullptr) != CUDA_SUCCESS)
+  if (g_drv.launch((CUfunction)fn, grid, 1, 1, p->cfg.block_threads, 1, 1, (unsigned)p->jit_smem, (CUstream)s,
+                   params, nullptr) != CUDA_SUCCESS)
     return PTAP_ERR_CUDA;
   return PTAP_OK;
 }

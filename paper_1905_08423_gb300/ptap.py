@@ -57,7 +57,7 @@ class _Config(_c.Structure):
                 ("visit_block_log2", _c.c_int32), ("specialize", _c.c_int32),
                 ("cache_indices", _c.c_int32), ("general_kernel", _c.c_int32),
                 ("compact_chunks", _c.c_int32), ("specialize_scope", _c.c_int32),
-                ("reserved", _c.c_int32 * 2)]
+                ("specialize_async", _c.c_int32), ("reserved", _c.c_int32 * 1)]
 
 
 class _Stats(_c.Structure):
@@ -210,7 +210,7 @@ class Csr:
 def make_config(mode=MODE_OWNER, chunk_entries=0, block_threads=0, group_lanes=0, ap_slots=0,
                 debug_checks=False, force_spill=False, class_programs=True,
                 visit_block_log2=0, specialize=False, cache_indices=False, general_kernel=0,
-                compact_chunks=False, specialize_in_batch=False) -> _Config:
+                compact_chunks=False, specialize_in_batch=False, specialize_async=False) -> _Config:
     cfg = _Config()
     cfg.mode = mode
     cfg.chunk_entries = chunk_entries
@@ -226,6 +226,7 @@ def make_config(mode=MODE_OWNER, chunk_entries=0, block_threads=0, group_lanes=0
     cfg.general_kernel = int(general_kernel)
     cfg.compact_chunks = 1 if compact_chunks is True else int(compact_chunks)
     cfg.specialize_scope = 1 if specialize_in_batch else 0
+    cfg.specialize_async = int(bool(specialize_async))
     return cfg
 
 

@@ -11,7 +11,7 @@ import torch
 import oracle
 from paper_1905_08423_gb300 import problems as pb
 from paper_1905_08423_gb300 import ptap
-from parity import check_values, rounded, run_and_check, to_dev
+from parity import check_pattern, check_values, rounded, run_and_check, to_dev
 
 pytestmark = pytest.mark.gpu
 
@@ -409,3 +409,39 @@ def test_numeric_host(dtype, pinned):
     for Ak, hC in zip(ins, outs):
         Ar = rounded(Ak, dtype)
         check_values(hC, oracle.ptap(Ar, Pr).val, oracle.ptap_bound(Ar, Pr).val, dtype)
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
+def test_background_specialisation(dtype):
+    """specialize_async: ptap_symbolic returns before NVRTC finishes; numeric products run
+    the interpreter until the compiled kernel is loaded, then switch to it; both agree with
+    the oracle."""
+    import time
+    A, P = pb.model_problem(33)
+    Ar, Pr = rounded(A, dtype), rounded(P, dtype)
+    ref, bound = oracle.ptap(Ar, Pr), oracle.ptap_bound(Ar, Pr)
+    dA, dP = to_dev(A, dtype), to_dev(P, dtype)
+    # a class count no other test compiles, so the compile is not already cached in the process
+    cfg = ptap.make_config(specialize=5, specialize_async=True, block_threads=512, chunk_entries=2048)
+    plan = ptap.symbolic(dA, dP, cfg)
+    check_pattern(plan, ref)
+    C = ptap.numeric(plan, dA, dP)           # interpreter or compiled, whichever is ready
+    torch.cuda.synchronize()
+    check_values(C, ref.val, bound.val, dtype)
+    t0 = time.time()
+    while plan.stats()["n_specialized"] == 0 and time.time() - t0 < 120:
+        time.sleep(0.05)
+    assert plan.stats()["n_specialized"] > 0, "the background compile did not finish"
+    C2 = ptap.numeric(plan, dA, dP)
+    torch.cuda.synchronize()
+    plan.check()
+    check_values(C2, ref.val, bound.val, dtype)
+    plan.destroy()
+
+
+def test_background_specialisation_destroy_while_compiling():
+    """Destroying a plan whose compile is still running waits for it; nothing leaks or faults."""
+    A, P = pb.model_problem(21)
+    dA, dP = to_dev(A, torch.float64), to_dev(P, torch.float64)
+    plan = ptap.symbolic(dA, dP, ptap.make_config(specialize=6, specialize_async=True, chunk_entries=1024))
+    plan.destroy()
