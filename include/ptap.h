@@ -106,10 +106,18 @@ typedef struct {
   int32_t specialize;     /* k > 0: compile straight-line code (NVRTC, at symbolic time) for
                              at most k classes covering most fine rows; 0 or -1: class
                              programs are interpreted */
-  int32_t cache_indices;  /* nonzero: the plan also stores, for every entry of A, the first
-                             position of P's row for its column (nnz(A) int32, a cached
-                             intermediate in the sense of Section 4.2), so the class-program
-                             kernels skip one dependent lookup per entry; 0: off */
+  int32_t cache_indices;  /* cached intermediates of the class-program kernels in the sense
+                             of Section 4.2 (memory traded for time):
+                             1: the plan stores, for every entry of A, the first position of
+                             P's row for its column (nnz(A) int32), so the kernels skip one
+                             dependent lookup per entry;
+                             2: the plan stores per visit of a fine row to a chunk, in
+                             warp-sized lane-major records, those positions for the row's
+                             entries of A and the accumulator offsets of its P(I,:) rows
+                             (int32 and uint16 per lane), so the kernels read them with
+                             coalesced loads and skip P(I,:)'s column lookups; plans with
+                             compact chunks, or records past 32 GB, fall back to 1;
+                             0: off */
   int32_t general_kernel; /* general owner-mode kernel (rows outside the class programs):
                              0 = sort-based, one warp per fine row (default);
                              1 = hash tables per group of group_lanes lanes */
@@ -160,6 +168,9 @@ typedef struct {
   int32_t specialized_permille; /* share of fine-row visits they cover, in 1/1000 */
   int32_t specialize_us;     /* time spent generating and compiling that code */
   int32_t compact_chunks;    /* 1 if the chunks are grown regions of C's graph */
+  int32_t cache_indices;     /* cached indices the plan holds: 0 none, 1 per entry of A,
+                                2 per visit (piece records) */
+  int64_t cached_index_bytes; /* device bytes of those cached indices (in plan_bytes) */
 } ptap_stats;
 
 typedef struct ptap_plan ptap_plan;

@@ -47,9 +47,11 @@ def candidate_list(fast_path: bool, n_classes: int, value_bytes: int, smem_optin
     plans: CTAs of 512 and 1024 threads, each with the largest chunk the
     accumulator allows and smaller ones (fewer entries per CTA: more CTAs for
     the same C, more fine rows visiting two chunks), with and without the
-    cached P row start per entry of A, and plan-time
-    specialisation of the most visited 16 or 32 classes (fewer if the problem
-    has fewer), plus the interpreter alone.  For plans outside the class
+    cached P row start per entry of A, with the indices cached per visit
+    instead (piece records, which also let a chunk between the middle size
+    and the largest pay off), and plan-time specialisation of the most
+    visited 16 or 32 classes (fewer if the problem has fewer), plus the
+    interpreter alone.  For plans outside the class
     programs: the sort-based and the hash-group general kernels over lanes per
     fine row, hash slots and chunk sizes (class-program plans try the default
     general kernel only).  The atomic scheme closes both lists.
@@ -64,9 +66,19 @@ def candidate_list(fast_path: bool, n_classes: int, value_bytes: int, smem_optin
             for ch in chunks:
                 for k in spec:
                     out.append(dict(specialize=k, block_threads=bt, chunk_entries=ch))
-            # the plan's cached index (Section 4.2's memory-for-time trade), every chunk size
+            # the plan's cached indices (Section 4.2's memory-for-time trade), every chunk size:
+            # per entry of A, and per visit
             for ch in chunks:
                 out.append(dict(specialize=spec[-1], block_threads=bt, chunk_entries=ch, cache_indices=True))
+            # per visit: only with the CTA size the compiled code is built to keep resident
+            # (1024 threads for 4-byte values, 512 for 8-byte ones, whose code holds twice
+            # the registers)
+            if bt == (1024 if value_bytes <= 4 else 512):
+                rec_chunks = sorted(set(chunks) | ({(mid + lim) // 2 & ~4095} if lim > mid + 4096 else set()),
+                                    reverse=True)
+                for ch in rec_chunks:
+                    out.append(dict(specialize=spec[-1], block_threads=bt, chunk_entries=ch,
+                                    cache_indices="visits"))
         out.append(dict())                                    # interpreter, 256 threads
         out.append(dict(block_threads=1024, chunk_entries=lim))  # interpreter, large CTAs
     out.append(dict(class_programs=False))                   # sort-based general kernel
@@ -211,8 +223,8 @@ def batch_candidate_list(value_bytes: int, smem_optin: int) -> list:
 
     The interpreter at 256 threads; batch-wide specialisation of the 32 or 64
     most visited class programs over the whole batch (compiled once, when the
-    batch is created) at 256, 512 and 1024 threads with the chunks each allows;
-    and the general kernel.
+    batch is created) at 256, 512 and 1024 threads with the chunks each allows,
+    and with the indices cached per visit; and the general kernel.
     """
     lim = chunk_limit(value_bytes, smem_optin)
     out = [dict()]
@@ -221,6 +233,10 @@ def batch_candidate_list(value_bytes: int, smem_optin: int) -> list:
         out.append(dict(specialize=k, specialize_in_batch=True, block_threads=512,
                         chunk_entries=max(1024, lim // 2)))
         out.append(dict(specialize=k, specialize_in_batch=True, block_threads=1024, chunk_entries=lim))
+    # indices cached per visit (piece records)
+    out.append(dict(specialize=64, specialize_in_batch=True, cache_indices="visits"))
+    out.append(dict(specialize=64, specialize_in_batch=True, block_threads=1024, chunk_entries=lim,
+                    cache_indices="visits"))
     out.append(dict(class_programs=False))
     return out
 

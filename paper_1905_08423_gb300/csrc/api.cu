@@ -52,7 +52,7 @@ Config resolve_config(const ptap_config* c) {
   r.group_lanes = (g == 4 || g == 8 || g == 16 || g == 32) ? g : r.group_lanes;
   r.ap_slots = std::min(std::max(pick(c->ap_slots, r.ap_slots), 4), 1024);
   r.debug_checks = c->debug_checks != 0;
-  r.cache_indices = c->cache_indices > 0 ? 1 : 0;
+  r.cache_indices = c->cache_indices >= 2 ? 2 : c->cache_indices > 0 ? 1 : 0;
   r.general_kernel = c->general_kernel == 1 ? 1 : 0;
   r.compact_chunks = std::max(0, std::min(c->compact_chunks, 4096));
   r.force_spill = c->force_spill != 0;
@@ -103,6 +103,8 @@ int ptap_plan_stats(const ptap_plan* p, ptap_stats* o) {
   o->specialized_permille = jit ? (int32_t)(p->jit_coverage * 1000.0 + 0.5) : 0;
   o->specialize_us = (int32_t)std::min(p->jit_ms * 1000.0, 2.0e9);
   o->compact_chunks = p->compact ? 1 : 0;
+  o->cache_indices = p->index_mode();
+  o->cached_index_bytes = p->rec ? p->rec_bytes + 4 * p->npieces : p->aq ? 4 * p->nnz_a : 0;
   return PTAP_OK;
 }
 

@@ -58,7 +58,7 @@ __global__ void __launch_bounds__(256) k_batch_owner(const NumArgs<V>* __restric
 struct NoSpecial {
   template <typename V>
   __device__ bool operator()(const ptapk::FastArgs<V>&, int32_t, int32_t, int32_t, int32_t, int32_t, V*,
-                             const int32_t*, int32_t) const {
+                             const int32_t*, int32_t, const int32_t*) const {
     return false;
   }
 };
@@ -188,6 +188,8 @@ int prepare_fast_side(ptap_batch* b, const std::vector<ptap_plan*>& fp, const st
     f.rs_global = nullptr;
     f.jit_slot = b->jit_fn ? slots[i] : nullptr;
     f.aq = p->aq;
+    f.rec = p->rec;
+    f.rec_off = p->rec_off;
     f.crows = p->compact ? p->chunk_crows : nullptr;
     f.row_loc = p->compact ? p->row_loc : nullptr;
     f.chunk_nnz = p->compact ? p->chunk_nnz : nullptr;

@@ -267,6 +267,13 @@ struct ptap_plan {
   void* jit_rs = nullptr;  // global scratch for the interpreted classes' rows of A P
   int32_t* jit_slot = nullptr;  // [nclasses] compiled-code number of each class, or -1
   int32_t* aq = nullptr;        // [nnz(A)] P.rp[A.ci[e]] when indices are cached
+  // piece records (indices cached per visit, lane-major; fastkern.cuh has
+  // the layout): record pc starts at rec + 4 * rec_off[pc]
+  int32_t* rec = nullptr;
+  int32_t* rec_off = nullptr;
+  int64_t rec_bytes = 0;
+  // 0: no cached indices, 1: aq, 2: piece records
+  int index_mode() const { return rec ? 2 : aq ? 1 : 0; }
   void* interp_rs = nullptr;  // the same for the interpreter kernel, when shared memory is short
   size_t jit_smem = 0;
   int jit_per_sm = 0, jit_classes = 0;

@@ -23,6 +23,7 @@ typedef unsigned int uint32_t;
 typedef long long int64_t;
 typedef unsigned long long uint64_t;
 typedef unsigned char uint8_t;
+typedef unsigned short uint16_t;
 typedef decltype(sizeof(0)) size_t;
 #else
 #include <stdint.h>
@@ -72,6 +73,16 @@ struct FastArgs {
   // Optional cached index: aq[e] = P.rp[A.ci[e]] for every entry e of A
   // (null: looked up through A.ci).
   const int32_t* aq;
+  // Optional piece records (cached per visit instead of per entry of A):
+  // piece pc's record starts at rec + 4 * rec_off[pc] and holds, lane-major,
+  //   q[x * 32 + lane] = P.rp[A.ci[A.rp[I] + x]]   for x < na       (int32)
+  //   o[s * 32 + lane] = accumulator offset of the row P.ci[P.rp[I] + s] in
+  //                      the piece's chunk, 0xFFFF outside it or past the
+  //                      piece's rows                   for s < pI       (uint16)
+  // for the lane's fine row I, so a warp reads them with coalesced loads.
+  // Null: aq, or A.ci and P's row starts.  Range chunks only.
+  const int32_t* rec;
+  const int32_t* rec_off;
   // Optional compact chunks.  When row_loc is set, the coarse rows of chunk c
   // are crows[chunk_row[c] .. chunk_row[c+1]) (ascending), row_loc[i] =
   // chunk << loc_bits | offset of row i's first entry in that chunk's
@@ -124,7 +135,7 @@ __device__ __forceinline__ void interp_add(double* p, double w, double r) {
 template <typename V>
 __device__ __forceinline__ void fast_piece(const FastArgs<V>& a, const uint8_t* prog, V* R, int32_t f,
                                            int32_t f1, int32_t i0, int32_t i1, V* acc,
-                                           const int32_t* roff, int32_t I) {
+                                           const int32_t* roff, int32_t I, const int32_t* rec) {
   const int lane = threadIdx.x & 31;
   const bool valid = f + lane < f1;
   // lanes past the piece's end redo its first row (I) and add nothing
@@ -141,13 +152,14 @@ __device__ __forceinline__ void fast_piece(const FastArgs<V>& a, const uint8_t* 
 #pragma unroll
     for (int j = 0; j < 4; ++j)
       if (x0 + j < na) {
-        if (!a.aq) k[j] = a.A.ci[ra + x0 + j];
+        if (!a.aq && !rec) k[j] = a.A.ci[ra + x0 + j];
         av[j] = a.A.val[ra + x0 + j];
       }
     int32_t pb[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j)
-      if (x0 + j < na) pb[j] = a.aq ? a.aq[ra + x0 + j] : a.P.rp[k[j]];
+      if (x0 + j < na)
+        pb[j] = rec ? rec[(x0 + j) * 32 + lane] : a.aq ? a.aq[ra + x0 + j] : a.P.rp[k[j]];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       if (x0 + j >= na) break;
@@ -174,9 +186,12 @@ __device__ __forceinline__ void fast_piece(const FastArgs<V>& a, const uint8_t* 
     cb[s] = -1;
     ws[s] = V(0);
     if (s < pI) {
-      const int32_t i = a.P.ci[rp + s];
       ws[s] = a.P.val[rp + s];
-      if (valid) {
+      if (rec) {
+        const int32_t o = ((const uint16_t*)(rec + na * 32))[s * 32 + lane];
+        if (o != 0xFFFF) cb[s] = o;
+      } else if (valid) {
+        const int32_t i = a.P.ci[rp + s];
         if (a.row_loc) {
           const int32_t l = a.row_loc[i];
           if ((l >> a.loc_bits) == i0) cb[s] = l & ((1 << a.loc_bits) - 1);
@@ -233,10 +248,11 @@ struct FastSmem {
   }
 };
 
-// One chunk c of a product.  `special(a, cls, f, f1, i0, i1, acc, roff, I)`
-// runs a piece of a class it has straight-line code for and returns true;
-// otherwise the interpreter runs it from the class's program.  I is the
-// lane's fine row of the piece, loaded one piece ahead.  With compact chunks
+// One chunk c of a product.  `special(a, slot, f, f1, i0, i1, acc, roff, I, rec)`
+// runs a piece whose class has compiled code number `slot` (jit_slot of its
+// class, -1 for none) and returns true; otherwise the interpreter runs it from
+// the class's program.  slot, the lane's fine row I and the piece's record
+// rec (or null) are loaded one piece ahead.  With compact chunks
 // i0 is the chunk number and the values go back to C row by row.
 template <typename V, typename Special>
 __device__ __forceinline__ void fast_chunk(const FastArgs<V>& a, int32_t c, FastSmem<V>& sm,
@@ -266,7 +282,7 @@ __device__ __forceinline__ void fast_chunk(const FastArgs<V>& a, int32_t c, Fast
   int32_t pc = a.chunk_piece[c] + warp;
   // software pipeline over this warp's pieces: the descriptor two pieces
   // ahead and the fine row one piece ahead are loaded while a piece runs
-  int32_t meta = 0, f0 = 0, metan = 0, f0n = 0, I = 0;
+  int32_t meta = 0, f0 = 0, metan = 0, f0n = 0, I = 0, ro = 0;
   if (pc < pe) {
     meta = a.piece_meta[pc];
     f0 = a.piece_f0[pc];
@@ -275,16 +291,26 @@ __device__ __forceinline__ void fast_chunk(const FastArgs<V>& a, int32_t c, Fast
     metan = a.piece_meta[pc + nwarps];
     f0n = a.piece_f0[pc + nwarps];
   }
-  if (pc < pe) I = a.frows[f0 + lane < f0 + (meta & 63) ? f0 + lane : f0];
+  int32_t sl = -1;
+  if (pc < pe) {
+    I = a.frows[f0 + lane < f0 + (meta & 63) ? f0 + lane : f0];
+    if (a.rec) ro = a.rec_off[pc];
+    if (a.jit_slot) sl = a.jit_slot[meta >> 6];
+  }
   for (; pc < pe; pc += nwarps) {
-    int32_t In = 0, metann = 0, f0nn = 0;
-    if (pc + nwarps < pe) In = a.frows[f0n + lane < f0n + (metan & 63) ? f0n + lane : f0n];
+    int32_t In = 0, metann = 0, f0nn = 0, ron = 0, sln = -1;
+    if (pc + nwarps < pe) {
+      In = a.frows[f0n + lane < f0n + (metan & 63) ? f0n + lane : f0n];
+      if (a.rec) ron = a.rec_off[pc + nwarps];
+      if (a.jit_slot) sln = a.jit_slot[metan >> 6];
+    }
     if (pc + 2 * nwarps < pe) {
       metann = a.piece_meta[pc + 2 * nwarps];
       f0nn = a.piece_f0[pc + 2 * nwarps];
     }
     const int32_t cls = meta >> 6, f1 = f0 + (meta & 63);
-    if (!special(a, cls, f0, f1, i0, i1, acc, roff, I)) {
+    const int32_t* rec = a.rec ? a.rec + 4 * (size_t)ro : nullptr;
+    if (!special(a, sl, f0, f1, i0, i1, acc, roff, I, rec)) {
       if (cls != loaded) {
         __syncwarp();
         const uint8_t* src = a.pool + a.class_off[cls];
@@ -292,13 +318,15 @@ __device__ __forceinline__ void fast_chunk(const FastArgs<V>& a, int32_t c, Fast
         __syncwarp();
         loaded = cls;
       }
-      fast_piece<V>(a, sm.prog, sm.Rs, f0, f1, i0, i1, acc, roff, I);
+      fast_piece<V>(a, sm.prog, sm.Rs, f0, f1, i0, i1, acc, roff, I, rec);
     }
     meta = metan;
     f0 = f0n;
     metan = metann;
     f0n = f0nn;
     I = In;
+    ro = ron;
+    sl = sln;
   }
   __syncthreads();
   if (compact) {

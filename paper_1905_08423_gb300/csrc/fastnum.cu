@@ -17,7 +17,7 @@ namespace {
 struct NoSpecial {
   template <typename V>
   __device__ bool operator()(const FastArgs<V>&, int32_t, int32_t, int32_t, int32_t, int32_t, V*,
-                             const int32_t*, int32_t) const {
+                             const int32_t*, int32_t, const int32_t*) const {
     return false;
   }
 };
@@ -54,6 +54,8 @@ static FastArgs<V> fast_args(ptap_plan* p, const ptap_csr* A, const ptap_csr* P,
   a.rs_global = (V*)p->interp_rs;
   a.jit_slot = p->jit_slot;
   a.aq = p->aq;
+  a.rec = p->rec;
+  a.rec_off = p->rec_off;
   a.crows = p->compact ? p->chunk_crows : nullptr;
   a.row_loc = p->compact ? p->row_loc : nullptr;
   a.chunk_nnz = p->compact ? p->chunk_nnz : nullptr;
@@ -141,8 +143,88 @@ __global__ void k_index_cache(const int32_t* __restrict__ Aci, const int32_t* __
     aq[e] = Prp[Aci[e]];
 }
 
+// Piece records (the indices cached per visit): the size of each piece's
+// record in 16-byte units, na int32 and pI uint16 per lane.
+__global__ void k_rec_sizes(const int32_t* __restrict__ meta, const uint8_t* __restrict__ pool,
+                            const int32_t* __restrict__ class_off, int64_t npieces, int32_t* __restrict__ size16) {
+  for (int64_t pc = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; pc < npieces;
+       pc += (int64_t)gridDim.x * blockDim.x) {
+    const uint8_t* g = pool + class_off[meta[pc] >> 6];
+    size16[pc] = g[0] * 8 + g[2] * 4;
+  }
+}
+
+// Fills the records, one warp per piece, the chunks strided over the grid:
+// per lane the row starts of P for the entries of A(I,:), and the accumulator
+// offset of each P(I,s)'s row in the piece's chunk (0xFFFF when the row lies
+// outside it, or the lane is past the piece's rows).
+__global__ void k_rec_fill(CsrI A, CsrI P, const int32_t* __restrict__ c_rp, const int32_t* __restrict__ chunk_row,
+                           const int32_t* __restrict__ chunk_piece, const int32_t* __restrict__ piece_f0,
+                           const int32_t* __restrict__ piece_meta, const int32_t* __restrict__ frows,
+                           const uint8_t* __restrict__ pool, const int32_t* __restrict__ class_off,
+                           const int32_t* __restrict__ rec_off, int32_t nchunks, int32_t* __restrict__ rec) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int32_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
+    const int32_t i0 = chunk_row[c], i1 = chunk_row[c + 1], base = c_rp[i0];
+    for (int32_t pc = chunk_piece[c] + warp; pc < chunk_piece[c + 1]; pc += nw) {
+      const int32_t meta = piece_meta[pc], f0 = piece_f0[pc];
+      const bool valid = lane < (meta & 63);
+      const int32_t I = frows[f0 + (valid ? lane : 0)];
+      const uint8_t* g = pool + class_off[meta >> 6];
+      const int na = g[0], pI = g[2];
+      int32_t* q = rec + 4 * (int64_t)rec_off[pc];
+      const int32_t ra = A.rp[I];
+      for (int x = 0; x < na; ++x) q[x * 32 + lane] = P.rp[A.ci[ra + x]];
+      uint16_t* o = (uint16_t*)(q + na * 32);
+      const int32_t rp = P.rp[I];
+      for (int t = 0; t < pI; ++t) {
+        const int32_t i = P.ci[rp + t];
+        o[t * 32 + lane] = valid && i >= i0 && i < i1 ? (uint16_t)(c_rp[i] - base) : (uint16_t)0xFFFF;
+      }
+    }
+  }
+}
+
+// Piece records for a class-program plan with range chunks; *done says
+// whether they were built (not when the chunks are compact, the offsets would
+// not fit 16 bits, or the records would pass 32 GB).
+static int build_records(ptap_plan* p, const ptap_csr* A, const ptap_csr* P, cudaStream_t s, bool* done) {
+  *done = false;
+  if (p->compact || p->cfg.chunk_entries > 0xFFFF || p->npieces <= 0) return PTAP_OK;
+  Scratch sc(&p->mem);
+  int32_t* size16 = nullptr;
+  PTAP_TRY(sc.get(&size16, p->npieces));
+  const int grid = (int)std::min<int64_t>(ceil_div(p->npieces, 256), (int64_t)num_sms() * 8);
+  k_rec_sizes<<<grid, 256, 0, s>>>(p->piece_meta, p->class_pool, p->class_off, p->npieces, size16);
+  PTAP_LAUNCHED();
+  PTAP_TRY(p->mem.get_n(&p->rec_off, p->npieces));
+  int64_t total16 = 0;
+  const int rc = exclusive_scan(p->mem, size16, p->rec_off, p->npieces, &total16, s);
+  if (rc == PTAP_ERR_OVERFLOW) {
+    p->mem.put(p->rec_off);
+    p->rec_off = nullptr;
+    return PTAP_OK;
+  }
+  PTAP_TRY(rc);
+  PTAP_TRY(p->mem.get((void**)&p->rec, (size_t)std::max<int64_t>(total16, 1) * 16));
+  k_rec_fill<<<num_sms() * 4, 256, 0, s>>>(CsrI{A->nrows, A->ncols, A->row_ptr, A->col_idx},
+                                           CsrI{P->nrows, P->ncols, P->row_ptr, P->col_idx}, p->c_rp,
+                                           p->chunk_row, p->chunk_piece, p->piece_f0, p->piece_meta,
+                                           p->chunk_frows, p->class_pool, p->class_off, p->rec_off, p->nchunks,
+                                           (int32_t*)p->rec);
+  PTAP_LAUNCHED();
+  p->rec_bytes = total16 * 16;
+  *done = true;
+  return PTAP_OK;
+}
+
 int build_index_cache(ptap_plan* p, const ptap_csr* A, const ptap_csr* P, cudaStream_t s) {
-  if (!p->fast || !p->cfg.cache_indices || p->aq || p->nnz_a == 0) return PTAP_OK;
+  if (!p->fast || !p->cfg.cache_indices || p->aq || p->rec || p->nnz_a == 0) return PTAP_OK;
+  if (p->cfg.cache_indices == 2) {
+    bool done = false;
+    PTAP_TRY(build_records(p, A, P, s, &done));
+    if (done) return PTAP_OK;
+  }
   PTAP_TRY(p->mem.get_n(&p->aq, p->nnz_a));
   k_index_cache<<<num_sms() * 8, 256, 0, s>>>(A->col_idx, P->row_ptr, p->nnz_a, p->aq);
   PTAP_LAUNCHED();

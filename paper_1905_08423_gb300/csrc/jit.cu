@@ -179,7 +179,7 @@ void appendf(std::string& o, const char* fmt, ...) {
 // at offsets sigma(s, t) read from a per-class constant table (Alg. 8).  The
 // loop keeps the code of a class near r accumulations instead of r * pI: the
 // instruction cache, not the issue rate, limits how many classes pay off.
-std::string gen_class(int cls, const uint8_t* g, bool cached, int loc_bits) {
+std::string gen_class(int cls, const uint8_t* g, int cached, int loc_bits) {
   const int na = g[0], r = g[1], pI = g[2];
   const uint8_t* pa = g + 8;
   const uint8_t* tsec = g + 8 + ((na + 7) & ~7);
@@ -191,14 +191,18 @@ std::string gen_class(int cls, const uint8_t* g, bool cached, int loc_bits) {
   o += "};\n";
   appendf(o,
           "__device__ __forceinline__ void cls_%d(const FastArgs<V>& a, int32_t f, int32_t f1, int32_t i0,"
-          " int32_t i1, V* acc, const int32_t* roff, int32_t I) {\n",
+          " int32_t i1, V* acc, const int32_t* roff, int32_t I, const int32_t* rec) {\n",
           cls);
   o += "  const int lane = threadIdx.x & 31;\n  const bool valid = f + lane < f1;\n"
        "  const int32_t ra = a.A.rp[I];\n"
-       "  const int32_t* Aci = a.A.ci + ra;\n  const V* Av = a.A.val + ra;\n  const V* Pv = a.P.val;\n";
-  if (cached) o += "  const int32_t* Aq = a.aq + ra;\n  (void)Aci;\n";
+       "  const int32_t* Aci = a.A.ci + ra;\n  const V* Av = a.A.val + ra;\n  const V* Pv = a.P.val;\n"
+       "  (void)rec;\n";
+  if (cached == 1) o += "  const int32_t* Aq = a.aq + ra;\n  (void)Aci;\n";
+  if (cached == 2) o += "  const int32_t* Rq = rec + lane;\n  (void)Aci;\n";
   for (int x = 0; x < na; ++x) {
-    if (cached)
+    if (cached == 2)
+      appendf(o, "  const V a%d = Av[%d];\n  const int32_t q%d = Rq[%d];\n", x, x, x, x * 32);
+    else if (cached == 1)
       appendf(o, "  const V a%d = Av[%d];\n  const int32_t q%d = Aq[%d];\n", x, x, x, x);
     else
       appendf(o, "  const V a%d = Av[%d];\n  const int32_t q%d = a.P.rp[Aci[%d]];\n", x, x, x, x);
@@ -223,6 +227,18 @@ std::string gen_class(int cls, const uint8_t* g, bool cached, int loc_bits) {
             "    if (valid && (l >> %d) == i0) {\n      V* c = acc + (l & %d);\n"
             "      const unsigned char* sg = sg_%d + s * %d;\n",
             pI, pI, loc_bits, (1 << loc_bits) - 1, cls, r);
+  } else if (cached == 2) {
+    // the piece's record gives each lane's accumulator offsets (0xFFFF: none)
+    appendf(o, "  const uint16_t* Ro = (const uint16_t*)(rec + %d) + lane;\n", na * 32);
+    o += "  int32_t on = Ro[0];\n  V wn = a.P.val[rp];\n  (void)valid;\n  (void)i0;\n  (void)i1;\n"
+         "  (void)roff;\n";
+    appendf(o,
+            "#pragma unroll 1\n  for (int s = 0; s < %d; ++s) {\n"
+            "    const int32_t ofs = on;\n    const V w = wn;\n"
+            "    if (s + 1 < %d) {\n      on = Ro[(s + 1) * 32];\n      wn = a.P.val[rp + s + 1];\n    }\n"
+            "    if (ofs != 0xFFFF) {\n      V* c = acc + ofs;\n"
+            "      const unsigned char* sg = sg_%d + s * %d;\n",
+            pI, pI, cls, r);
   } else {
     o += "  int32_t in = a.P.ci[rp];\n  V wn = a.P.val[rp];\n";
     appendf(o,
@@ -276,17 +292,17 @@ int read_classes(ptap_plan* p, ClassTable& t) {
 // Source of a specialised kernel for the programs `hot` (in this order: the
 // compiled-code numbers are positions in it).  kind 0: one product
 // (ptap_jit_numeric); kind 1: a batch of products (ptap_jit_batch).
-std::string build_source(int dtype, const std::vector<std::string>& hot, bool cached, int loc_bits,
+std::string build_source(int dtype, const std::vector<std::string>& hot, int cached, int loc_bits,
                          int block_threads, int kind) {
   std::string src = "#include \"fastkern.cuh\"\nusing namespace ptapk;\n";
   src += dtype == PTAP_F64 ? "typedef double V;\n" : "typedef float V;\n";
   for (size_t i = 0; i < hot.size(); ++i)
     src += gen_class((int)i, (const uint8_t*)hot[i].data(), cached, loc_bits);
-  src += "struct Special {\n  __device__ bool operator()(const FastArgs<V>& a, int32_t cls, int32_t f, int32_t f1,"
-         " int32_t i0, int32_t i1, V* acc, const int32_t* roff, int32_t I) const {\n"
-         "    switch (a.jit_slot[cls]) {\n";
+  src += "struct Special {\n  __device__ bool operator()(const FastArgs<V>& a, int32_t slot, int32_t f, int32_t f1,"
+         " int32_t i0, int32_t i1, V* acc, const int32_t* roff, int32_t I, const int32_t* rec) const {\n"
+         "    switch (slot) {\n";
   for (size_t i = 0; i < hot.size(); ++i)
-    appendf(src, "      case %d: cls_%d(a, f, f1, i0, i1, acc, roff, I); return true;\n", (int)i, (int)i);
+    appendf(src, "      case %d: cls_%d(a, f, f1, i0, i1, acc, roff, I, rec); return true;\n", (int)i, (int)i);
   src += "      default: return false;\n    }\n  }\n};\n";
   // FP32: 64 registers a thread, 1024 resident threads per SM.  FP64 code
   // holds twice the bytes in registers and spills at 64; 128 registers with
@@ -446,7 +462,7 @@ int jit_prepare(ptap_plan* p) {
   std::sort(hot.begin(), hot.end(), [&](int x, int y) { return t.bytes(x) < t.bytes(y); });
   std::vector<std::string> progs;
   for (int k : hot) progs.push_back(t.bytes(k));
-  std::string src = build_source(p->dtype, progs, p->aq != nullptr, p->compact ? p->loc_bits : 0,
+  std::string src = build_source(p->dtype, progs, p->index_mode(), p->compact ? p->loc_bits : 0,
                                  p->cfg.block_threads, 0);
   // Resources the launch needs, sized before the compile (on this thread:
   // the allocator is not shared with the background thread).  The scratch
@@ -493,7 +509,7 @@ int jit_launch(ptap_plan* p, void* fn, const void* args, int grid, cudaStream_t 
 // share one compiled body), visits are summed over the plans, and the most
 // visited `max_classes` programs are compiled into ptap_jit_batch.  For each
 // plan, slots[q] receives a device table (from `mem`) mapping its class ids
-// to compiled numbers or -1.  All plans must agree on cached indices; compact
+// to compiled numbers or -1.  All plans must agree on the cached indices; compact
 // chunks are not specialised.
 int jit_prepare_batch(ptap_plan* const* plans, int count, int max_classes, int threads, Tracker& mem,
                       cudaStream_t s, void** fn_out, std::vector<int32_t*>& slots, int* nhot,
@@ -501,13 +517,13 @@ int jit_prepare_batch(ptap_plan* const* plans, int count, int max_classes, int t
   std::lock_guard<std::mutex> lock(g_mu);
   load_apis();
   if (!g_rtc.ok || !g_drv.ok || count <= 0) return PTAP_ERR_UNSUPPORTED;
-  const bool cached = plans[0]->aq != nullptr;
+  const int cached = plans[0]->index_mode();
   std::vector<ClassTable> tabs(count);
   std::map<std::string, int64_t> pooled;
   int64_t total = 0;
   for (int q = 0; q < count; ++q) {
     ptap_plan* p = plans[q];
-    if (!p->fast || p->compact || (p->aq != nullptr) != cached || p->nclasses <= 0) return PTAP_ERR_UNSUPPORTED;
+    if (!p->fast || p->compact || p->index_mode() != cached || p->nclasses <= 0) return PTAP_ERR_UNSUPPORTED;
     PTAP_TRY(read_classes(p, tabs[q]));
     for (int k = 0; k < p->nclasses; ++k) pooled[tabs[q].bytes(k)] += tabs[q].visits[k];
     total += tabs[q].total;

@@ -72,7 +72,8 @@ class _Stats(_c.Structure):
                 ("n_classes", _c.c_int32), ("n_segments", _c.c_int32),
                 ("n_pieces", _c.c_int32), ("n_specialized", _c.c_int32),
                 ("specialized_permille", _c.c_int32), ("specialize_us", _c.c_int32),
-                ("compact_chunks", _c.c_int32)]
+                ("compact_chunks", _c.c_int32), ("cache_indices", _c.c_int32),
+                ("cached_index_bytes", _c.c_int64)]
 
 
 _LIB = None
@@ -222,7 +223,7 @@ def make_config(mode=MODE_OWNER, chunk_entries=0, block_threads=0, group_lanes=0
     cfg.class_programs = 0 if class_programs else -1
     cfg.visit_block_log2 = visit_block_log2
     cfg.specialize = 8 if specialize is True else (-1 if not specialize else int(specialize))
-    cfg.cache_indices = int(bool(cache_indices))
+    cfg.cache_indices = 2 if cache_indices in ("visits", 2) else int(bool(cache_indices))
     cfg.general_kernel = int(general_kernel)
     cfg.compact_chunks = 1 if compact_chunks is True else int(compact_chunks)
     cfg.specialize_scope = 1 if specialize_in_batch else 0

@@ -2,8 +2,9 @@
 trilinear and smoothed-aggregation P) in one batched launch, against the oracle.
 
 Every product of the batch is checked on sampled coarse rows (Eq. 8 row form)
-within tau * (|P|^T|A||P|)(i,j), in FP32 and FP64, for the interpreter and for
-the batch-wide specialised kernel at the CTA sizes the batch tuner offers.  A
+within tau * (|P|^T|A||P|)(i,j), in FP32 and FP64, for every configuration
+the batch tuner offers (the interpreter, the batch-wide specialised kernel at
+each CTA size, with indices cached per visit, and the general kernel).  A
 CUDA graph that captured the batched launch is then replayed after every
 stored value of every A is rescaled in place by a factor drawn from
 U(0.5, 2), and all 64 products are checked again against the oracle on the
@@ -25,11 +26,11 @@ pytestmark = pytest.mark.gpu
 def _configs():
     props = torch.cuda.get_device_properties(0)
     optin = int(getattr(props, "shared_memory_per_block_optin", 232448))
-    out = {}
-    for vb, name in ((4, "f32"), (8, "f64")):
-        c = autotune.batch_candidate_list(vb, optin)
-        out[name] = [c[0], c[1], c[3], c[-1]]   # interpreter; specialised at 256 and 1024; general
-    return out
+    return {name: autotune.batch_candidate_list(vb, optin) for vb, name in ((4, "f32"), (8, "f64"))}
+
+
+# every candidate of the batch tuner (their number does not depend on the device)
+_N_CANDIDATES = len(autotune.batch_candidate_list(4, 232448))
 
 
 @pytest.fixture(scope="module")
@@ -53,7 +54,7 @@ def _check_all(probs, plans, Cs, dtype, seed):
 
 
 @pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
-@pytest.mark.parametrize("k", range(4))
+@pytest.mark.parametrize("k", range(_N_CANDIDATES))
 def test_batch64_every_product(batch64, dtype, k):
     cfg = _configs()["f32" if dtype == torch.float32 else "f64"][k]
     devs, plans, Cs, batch = _run(batch64, dtype, cfg)
@@ -67,7 +68,7 @@ def test_batch64_every_product(batch64, dtype, k):
 
 @pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
 def test_batch64_graph_replay_after_rescale(batch64, dtype):
-    cfg = _configs()["f32" if dtype == torch.float32 else "f64"][2]
+    cfg = _configs()["f32" if dtype == torch.float32 else "f64"][3]   # specialised, 1024 threads
     devs, plans, Cs, batch = _run(batch64, dtype, cfg)
     s = torch.cuda.Stream()
     s.wait_stream(torch.cuda.current_stream())

@@ -74,6 +74,9 @@ CONFIGS = [
     dict(class_programs=False, block_threads=64),  # sort-based general kernel, 2 warps a CTA
     dict(cache_indices=True),                     # cached P row starts, interpreter
     dict(cache_indices=True, specialize=4, chunk_entries=1024),  # ... and compiled classes
+    dict(cache_indices="visits"),                 # piece records, interpreter
+    dict(cache_indices="visits", specialize=4, chunk_entries=1024),  # ... and compiled classes
+    dict(cache_indices="visits", chunk_entries=64),  # records over many small chunks
 ]
 
 
@@ -83,6 +86,7 @@ LARGE_CTA = [
     dict(block_threads=1024, chunk_entries=32768),
     dict(block_threads=512, chunk_entries=12288),
     dict(specialize=8, block_threads=1024, chunk_entries=32768, cache_indices=True),
+    dict(specialize=8, block_threads=1024, chunk_entries=24576, cache_indices="visits"),
 ]
 
 
@@ -445,3 +449,22 @@ def test_background_specialisation_destroy_while_compiling():
     dA, dP = to_dev(A, torch.float64), to_dev(P, torch.float64)
     plan = ptap.symbolic(dA, dP, ptap.make_config(specialize=6, specialize_async=True, chunk_entries=1024))
     plan.destroy()
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_piece_records(dtype):
+    """Indices cached per visit: the plan holds piece records (one int32 per entry of A(I,:)
+    and one uint16 per entry of P(I,:) for every lane of every piece, plus an offset per
+    piece), the compiled and interpreted classes both read them, and C matches the oracle;
+    compact chunks fall back to the per-entry cache."""
+    A, P = pb.model_problem(31)
+    cfg = dict(cache_indices="visits", specialize=8, block_threads=1024, chunk_entries=8192)
+    plan, _ = run_and_check(A, P, dtype, ptap.make_config(**cfg))
+    st = plan.stats()
+    assert st["fast_path"] == 1 and st["cache_indices"] == 2 and st["n_specialized"] == 8
+    assert 0 < st["specialized_permille"] < 1000            # interpreted classes too
+    assert st["cached_index_bytes"] >= 4 * st["n_pieces"] + 2 * 32 * st["n_pieces"]
+    plan_c, _ = run_and_check(A, P, dtype, ptap.make_config(**dict(cfg, compact_chunks=1)))
+    stc = plan_c.stats()
+    assert stc["compact_chunks"] == 1 and stc["cache_indices"] == 1
+    assert stc["cached_index_bytes"] == 4 * A.nnz
