@@ -341,6 +341,13 @@ int compile_or_load(const std::string& src, const char* name, CUfunction* fn_out
   const std::string dir = cache_dir();
   char fname[64];
   snprintf(fname, sizeof fname, "jit_%016llx_sm103a.cubin", (unsigned long long)key);
+  // PTAP_JIT_SOURCE_DIR: also write the generated source there (jit_<key>.cu),
+  // for reading and for offline compiles of the same code
+  if (const char* sd = getenv("PTAP_JIT_SOURCE_DIR"); sd && *sd) {
+    char sname[64];
+    snprintf(sname, sizeof sname, "jit_%016llx.cu", (unsigned long long)key);
+    write_file_atomic(sd, sname, std::vector<char>(src.begin(), src.end()));
+  }
   std::vector<char> cached;
   if (it != g_cache.end()) {
     fn = it->second;
