@@ -50,7 +50,7 @@ def candidate_list(fast_path: bool, n_classes: int, value_bytes: int, smem_optin
     cached P row start per entry of A, with the indices cached per visit
     instead (piece records, which also let a chunk between the middle size
     and the largest pay off), and plan-time specialisation of the most
-    visited 16 or 32 classes (fewer if the problem has fewer), plus the
+    visited 32 or 64 classes (fewer if the problem has fewer), plus the
     interpreter alone.  For plans outside the class
     programs: the sort-based and the hash-group general kernels over lanes per
     fine row, hash slots and chunk sizes (class-program plans try the default
@@ -59,7 +59,7 @@ def candidate_list(fast_path: bool, n_classes: int, value_bytes: int, smem_optin
     out = []
     if fast_path:
         lim = chunk_limit(value_bytes, smem_optin)
-        spec = sorted({min(16, n_classes), min(32, n_classes)} - {0})
+        spec = sorted({min(32, n_classes), min(64, n_classes)} - {0})
         mid = 32768 if lim > 32768 else max(1024, (lim * 5 // 6) & ~4095)
         for bt in (1024, 512):
             chunks = sorted({lim, mid, max(1024, lim // 2)}, reverse=True)

@@ -214,7 +214,8 @@ __device__ __forceinline__ void fast_piece(const FastArgs<V>& a, const uint8_t* 
 
 // Shared-memory carve-up: accumulator | interpreter R rows (unless they live
 // in global scratch) | row offsets | per-warp program buffers; every region
-// 16-byte aligned.
+// 16-byte aligned.  max_rows = 0 with piece records, which carry the
+// accumulator offsets themselves.  What is not carved stays L1.
 template <typename V>
 __host__ __device__ inline size_t fast_smem_bytes(int CH, int threads, int maxr, int max_rows,
                                                   int prog_cap, bool rs_in_smem = true) {
@@ -273,7 +274,7 @@ __device__ __forceinline__ void fast_chunk(const FastArgs<V>& a, int32_t c, Fast
     nnz = a.c_rp[i1] - base;
   }
   for (int t = threadIdx.x; t < nnz; t += blockDim.x) acc[t] = V(0);
-  if (!compact)
+  if (!compact && !a.rec)
     for (int t = threadIdx.x; t <= i1 - i0; t += blockDim.x) roff[t] = a.c_rp[i0 + t] - base;
   __syncthreads();
   // the chunk's pieces (<= 32 rows of one class) go round-robin to the warps

@@ -69,8 +69,14 @@ static size_t fast_smem(const ptap_plan* p, bool rs_in_smem = true) {
                                    std::max(p->max_chunk_rows, 1), (p->class_maxlen + 15) & ~15, rs_in_smem);
 }
 
-size_t fast_smem_for(const ptap_plan* p, bool rs_in_smem) {
-  return p->dtype == PTAP_F64 ? fast_smem<double>(p, rs_in_smem) : fast_smem<float>(p, rs_in_smem);
+// The specialised kernel's carve-up: the interpreted classes keep their rows
+// of A P in global scratch, and with piece records no row offsets are kept.
+size_t jit_smem_for(const ptap_plan* p) {
+  const int rows = p->rec ? 0 : std::max(p->max_chunk_rows, 1);
+  const int maxr = std::max(p->class_maxr, 1), cap = (p->class_maxlen + 15) & ~15;
+  return p->dtype == PTAP_F64
+             ? ptapk::fast_smem_bytes<double>(p->cfg.chunk_entries, p->cfg.block_threads, maxr, rows, cap, false)
+             : ptapk::fast_smem_bytes<float>(p->cfg.chunk_entries, p->cfg.block_threads, maxr, rows, cap, false);
 }
 
 // The dynamic schedule: chunks ordered by fine-row visits, longest first, and
@@ -253,6 +259,7 @@ static int launch_fast_t(ptap_plan* p, const ptap_csr* A, const ptap_csr* P, voi
     const int grid = (int)std::min<int64_t>(p->nchunks, (int64_t)num_sms() * p->jit_per_sm);
     if (grid <= 0) return PTAP_OK;
     args.rs_global = (V*)p->jit_rs;
+    if (p->rec) args.max_rows = 0;  // the carve-up of jit_smem_for
     return jit_launch(p, fn, &args, grid, s);
   }
   const int grid = (int)std::min<int64_t>(p->nchunks, (int64_t)num_sms() * p->num_per_sm);

@@ -42,7 +42,7 @@
 
 namespace ptap {
 
-size_t fast_smem_for(const ptap_plan* p, bool rs_in_smem);
+size_t jit_smem_for(const ptap_plan* p);
 
 namespace {
 
@@ -474,7 +474,7 @@ int jit_prepare(ptap_plan* p) {
   // Resources the launch needs, sized before the compile (on this thread:
   // the allocator is not shared with the background thread).  The scratch
   // takes the resident-CTA bound that the thread count allows.
-  p->jit_smem = fast_smem_for(p, false);
+  p->jit_smem = jit_smem_for(p);
   const int bound_per_sm = std::max(1, 2048 / p->cfg.block_threads);
   p->jit_per_sm = bound_per_sm;
   const size_t vb = p->dtype == PTAP_F64 ? 8 : 4;
