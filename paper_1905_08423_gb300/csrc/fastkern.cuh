@@ -313,9 +313,11 @@ __device__ __forceinline__ void fast_chunk(const FastArgs<V>& a, int32_t c, Fast
     const int32_t* rec = a.rec ? a.rec + 4 * (size_t)ro : nullptr;
     if (!special(a, sl, f0, f1, i0, i1, acc, roff, I, rec)) {
       if (cls != loaded) {
+        // programs start on 8-byte boundaries and the pool is padded past the
+        // longest, so the copy moves prog_cap bytes as 8-byte words
         __syncwarp();
-        const uint8_t* src = a.pool + a.class_off[cls];
-        for (int x = lane; x < a.prog_cap; x += 32) sm.prog[x] = src[x];
+        const uint2* src = (const uint2*)(a.pool + a.class_off[cls]);
+        for (int x = lane; x < a.prog_cap / 8; x += 32) ((uint2*)sm.prog)[x] = src[x];
         __syncwarp();
         loaded = cls;
       }
