@@ -441,6 +441,8 @@ def bench_algebraic(ptap, autotune, pb, dev, ev, s, steps, tuned_ok=True, fp64_p
            "symbolic_ms": round(e0.elapsed_time(e1), 2),
            "launch_config": cfg_kw, "fast_path": st["fast_path"], "classes": st["n_classes"],
            "specialized_classes": st["n_specialized"],
+           "candidates_ms": ([(c, round(v, 4) if isinstance(v, float) else v) for c, v in t.trials]
+                             if t else None),
            "two_step": {"ms_per_step": round(two_ms, 4), "speedup_all_at_once": round(two_ms / ms, 3),
                         "agrees_with_all_at_once": same},
            "peak_mb": {"all_at_once": round(peak / 2**20, 1), "two_step": round(two_peak / 2**20, 1),

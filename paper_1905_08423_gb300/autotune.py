@@ -11,7 +11,8 @@ the device's opt-in shared memory and the value size bound the on-chip
 accumulator (chunk entries) for each CTA size; the general kernels get their
 lanes per fine row, hash slots and chunk sizes, and the atomic scheme (Alg. 8
 taken literally) is always among them.  ``tune`` builds a plan per candidate,
-times repeated numeric products with CUDA events and returns the fastest.
+times repeated numeric products with CUDA events, tries more compiled classes
+for the two fastest, and returns the fastest.
 Choices are cached in a JSON file keyed by (GPU name, dtype, problem
 signature); the signature is the shapes, the nonzero counts and a hash of the
 row-length sequences of A and P.
@@ -40,36 +41,41 @@ def chunk_limit(value_bytes: int, smem_optin: int) -> int:
     return max(1024, min(_MAX_CHUNK, n & ~1023))
 
 
+def _spec_counts(n_classes: int) -> list:
+    """Compiled-class counts the tuner tries: 32, then 64 (fewer if the problem has fewer)."""
+    return sorted({min(32, n_classes), min(64, n_classes)} - {0})
+
+
 def candidate_list(fast_path: bool, n_classes: int, value_bytes: int, smem_optin: int) -> list:
-    """Candidate configurations (ptap.make_config keywords) for one problem.
+    """First-round candidate configurations (ptap.make_config keywords) for one problem.
 
     fast_path / n_classes come from a default symbolic pass.  For class-program
     plans: CTAs of 512 and 1024 threads, each with the largest chunk the
     accumulator allows and smaller ones (fewer entries per CTA: more CTAs for
-    the same C, more fine rows visiting two chunks), with and without the
-    cached P row start per entry of A, with the indices cached per visit
-    instead (piece records, which also let a chunk between the middle size
-    and the largest pay off), and plan-time specialisation of the most
-    visited 32 or 64 classes (fewer if the problem has fewer), plus the
-    interpreter alone.  For plans outside the class
-    programs: the sort-based and the hash-group general kernels over lanes per
-    fine row, hash slots and chunk sizes (class-program plans try the default
+    the same C, more fine rows visiting two chunks), without cached indices,
+    with the cached P row start per entry of A, and with the indices cached
+    per visit (piece records, which also let a chunk between the middle size
+    and the largest pay off), each with plan-time specialisation of the 32
+    most visited classes (fewer if the problem has fewer), plus the
+    interpreter alone.  ``refinements`` gives the second round (more compiled
+    classes for the best of these).  For plans outside the class programs:
+    the sort-based and the hash-group general kernels over lanes per fine
+    row, hash slots and chunk sizes (class-program plans try the default
     general kernel only).  The atomic scheme closes both lists.
     """
     out = []
     if fast_path:
         lim = chunk_limit(value_bytes, smem_optin)
-        spec = sorted({min(32, n_classes), min(64, n_classes)} - {0})
+        k = _spec_counts(n_classes)[0]
         mid = 32768 if lim > 32768 else max(1024, (lim * 5 // 6) & ~4095)
         for bt in (1024, 512):
             chunks = sorted({lim, mid, max(1024, lim // 2)}, reverse=True)
             for ch in chunks:
-                for k in spec:
-                    out.append(dict(specialize=k, block_threads=bt, chunk_entries=ch))
+                out.append(dict(specialize=k, block_threads=bt, chunk_entries=ch))
             # the plan's cached indices (Section 4.2's memory-for-time trade), every chunk size:
             # per entry of A, and per visit
             for ch in chunks:
-                out.append(dict(specialize=spec[-1], block_threads=bt, chunk_entries=ch, cache_indices=True))
+                out.append(dict(specialize=k, block_threads=bt, chunk_entries=ch, cache_indices=True))
             # per visit: only with the CTA size the compiled code is built to keep resident
             # (1024 threads for 4-byte values, 512 for 8-byte ones, whose code holds twice
             # the registers)
@@ -77,8 +83,7 @@ def candidate_list(fast_path: bool, n_classes: int, value_bytes: int, smem_optin
                 rec_chunks = sorted(set(chunks) | ({(mid + lim) // 2 & ~4095} if lim > mid + 4096 else set()),
                                     reverse=True)
                 for ch in rec_chunks:
-                    out.append(dict(specialize=spec[-1], block_threads=bt, chunk_entries=ch,
-                                    cache_indices="visits"))
+                    out.append(dict(specialize=k, block_threads=bt, chunk_entries=ch, cache_indices="visits"))
         out.append(dict())                                    # interpreter, 256 threads
         out.append(dict(block_threads=1024, chunk_entries=lim))  # interpreter, large CTAs
     out.append(dict(class_programs=False))                   # sort-based general kernel
@@ -89,18 +94,32 @@ def candidate_list(fast_path: bool, n_classes: int, value_bytes: int, smem_optin
                 out.append(dict(class_programs=False, general_kernel=1, chunk_entries=ch,
                                 group_lanes=g, ap_slots=slots))
     out.append(dict(mode=2, group_lanes=8, ap_slots=64))     # atomic scatter (Alg. 8)
-    # drop duplicates, keep order
+    return _unique(out)
+
+
+def refinements(cfg: dict, n_classes: int) -> list:
+    """Second-round candidates from a first-round one: the same launch with more
+    classes compiled (each costs compile time and instruction-cache room, so
+    whether it pays depends on the problem)."""
+    k = cfg.get("specialize")
+    if not k or k is True:
+        return []
+    return [dict(cfg, specialize=c) for c in _spec_counts(n_classes) if c > k]
+
+
+def _unique(cands: list) -> list:
+    """Drops duplicates, keeps order."""
     seen, uniq = set(), []
-    for c in out:
-        k = json.dumps(c, sort_keys=True)
-        if k not in seen:
-            seen.add(k)
+    for c in cands:
+        key = json.dumps(c, sort_keys=True)
+        if key not in seen:
+            seen.add(key)
             uniq.append(c)
     return uniq
 
 
-def candidates(A, P) -> list:
-    """Candidates for device matrices A, P (ptap.Csr), from one default symbolic pass."""
+def _problem(A, P):
+    """(fast_path, n_classes, value bytes, opt-in shared memory) from one default symbolic pass."""
     import torch
 
     from . import ptap
@@ -110,7 +129,20 @@ def candidates(A, P) -> list:
     props = torch.cuda.get_device_properties(A.row_ptr.device)
     optin = int(getattr(props, "shared_memory_per_block_optin", 232448))
     vb = 8 if A.dtype_code == ptap.F64 else 4
-    return candidate_list(bool(st["fast_path"]), int(st["n_classes"]), vb, optin)
+    return bool(st["fast_path"]), int(st["n_classes"]), vb, optin
+
+
+def candidates(A, P) -> list:
+    """First-round candidates for device matrices A, P (ptap.Csr)."""
+    return candidate_list(*_problem(A, P))
+
+
+def candidates_all(A, P) -> list:
+    """Every configuration ``tune`` may choose for A, P: the first round and the
+    refinements of each of its candidates."""
+    fast, n_classes, vb, optin = _problem(A, P)
+    first = candidate_list(fast, n_classes, vb, optin)
+    return _unique(first + [r for c in first for r in refinements(c, n_classes)])
 
 
 def signature(A, P) -> str:
@@ -171,8 +203,9 @@ def tune(A, P, candidates=None, reps: int = 5, warmup: int = 2, cache_path: str 
          use_cache: bool = True, slow_factor: float = 3.0) -> TuneResult:
     """Times each candidate configuration on the device matrices A, P (ptap.Csr).
 
-    ``candidates`` defaults to ``candidates(A, P)``.  Returns the fastest
-    configuration (keyword arguments of ptap.make_config).  A candidate whose
+    ``candidates`` defaults to ``candidates(A, P)``, followed by a second round:
+    the ``refinements`` (more compiled classes) of the two fastest.  Returns
+    the fastest configuration (keyword arguments of ptap.make_config).  A candidate whose
     first product takes more than ``slow_factor`` times the best so far is
     recorded with that one time and not repeated.  Candidates that fail (for
     example by exceeding shared memory) are skipped.
@@ -187,10 +220,14 @@ def tune(A, P, candidates=None, reps: int = 5, warmup: int = 2, cache_path: str 
     if use_cache and key in cache:
         e = cache[key]
         return TuneResult(dict(e["config"]), float(e["ms"]), [], cached=True)
+    n_classes = None
     if candidates is None:
-        candidates = globals()["candidates"](A, P)
+        fast, n_classes, vb, optin = _problem(A, P)
+        candidates = candidate_list(fast, n_classes, vb, optin)
     best, best_ms, trials, sym = None, float("inf"), [], []
-    for cand in candidates:
+
+    def run(cand):
+        nonlocal best, best_ms
         try:
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
@@ -205,10 +242,22 @@ def tune(A, P, candidates=None, reps: int = 5, warmup: int = 2, cache_path: str 
             del C
         except ptap.PtapError as e:
             trials.append((cand, str(e)))
-            continue
+            return
         trials.append((cand, ms))
         if ms < best_ms:
             best, best_ms = dict(cand), ms
+
+    for cand in candidates:
+        run(cand)
+    # second round (default candidates only): more compiled classes for the two fastest
+    if n_classes is not None:
+        timed = sorted((t for t in trials if isinstance(t[1], float)), key=lambda t: t[1])
+        seen = {json.dumps(c, sort_keys=True) for c, _ in trials}
+        for cand, _ in timed[:2]:
+            for r in refinements(cand, n_classes):
+                if json.dumps(r, sort_keys=True) not in seen:
+                    seen.add(json.dumps(r, sort_keys=True))
+                    run(r)
     if best is None:
         raise RuntimeError("no candidate configuration ran")
     if cache_path:

@@ -1,8 +1,9 @@
 """Full-size parity of every launch configuration the autotuner may choose.
 
 The benchmark times the configuration ``autotune.tune`` picks on its own
-workload.  The tuner picks among ``autotune.candidates(A, P)``, so checking
-every one of those candidates at full size covers whichever wins, on the same
+workload.  The tuner picks among ``autotune.candidates_all(A, P)`` (its first round and
+the second-round refinements of each), so checking every one of those at full
+size covers whichever wins, on the same
 inputs the benchmark uses: the 319^3 model problem (FP32 and FP64) and the
 200^3 algebraic case (FP64).  For each candidate the whole pattern is checked
 by its closed form and ~3,600 sampled coarse rows against the oracle's rows of
@@ -37,7 +38,7 @@ def model319():
 def _every_candidate(A, P, dtype, rows, lengths=None, nnz=None):
     dA, dP = to_dev(A, dtype), to_dev(P, dtype)
     ref, bnd = sampled_reference(A, P, dtype, rows)
-    cands = autotune.candidates(dA, dP)
+    cands = autotune.candidates_all(dA, dP)
     assert cands, "the tuner offered no candidate"
     checked = []
     for cand in cands:
