@@ -42,8 +42,12 @@ def chunk_limit(value_bytes: int, smem_optin: int) -> int:
 
 
 def _spec_counts(n_classes: int) -> list:
-    """Compiled-class counts the tuner tries: 32, then 64 (fewer if the problem has fewer)."""
-    return sorted({min(32, n_classes), min(64, n_classes)} - {0})
+    """Compiled-class counts the tuner tries: 16 in the first round, 32 and 64 in the second
+    (fewer if the problem has fewer).  More classes compiled means fewer interpreted visits
+    but more code competing for the instruction cache, and which wins depends on the problem:
+    64 on the 319^3 model problem (57 compiled, the 99% rule), 16 on the 200^3 algebraic one,
+    whose 27-entry rows of A make each class's code long."""
+    return sorted({min(16, n_classes), min(32, n_classes), min(64, n_classes)} - {0})
 
 
 def candidate_list(fast_path: bool, n_classes: int, value_bytes: int, smem_optin: int) -> list:
@@ -55,7 +59,7 @@ def candidate_list(fast_path: bool, n_classes: int, value_bytes: int, smem_optin
     the same C, more fine rows visiting two chunks), without cached indices,
     with the cached P row start per entry of A, and with the indices cached
     per visit (piece records, which also let a chunk between the middle size
-    and the largest pay off), each with plan-time specialisation of the 32
+    and the largest pay off), each with plan-time specialisation of the 16
     most visited classes (fewer if the problem has fewer), plus the
     interpreter alone.  ``refinements`` gives the second round (more compiled
     classes for the best of these).  For plans outside the class programs:

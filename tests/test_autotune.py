@@ -45,14 +45,14 @@ def test_tune_and_parity(tmp_path):
 
 
 def test_candidate_rounds():
-    """First round: every class-program launch with 32 compiled classes, with and without
+    """First round: every class-program launch with 16 compiled classes, with and without
     cached indices (per entry of A; per visit at the resident CTA size); second round: the
-    same launch with 64 classes, never fewer than the first, none for the interpreter."""
+    same launch with 32 and 64 classes, never fewer than the first, none for the interpreter."""
     optin = 232448
     for vb, bt in ((4, 1024), (8, 512)):
         first = autotune.candidate_list(True, 439, vb, optin)
         spec = {c["specialize"] for c in first if "specialize" in c}
-        assert spec == {32}
+        assert spec == {16}
         assert any(c.get("cache_indices") is True for c in first)
         visits = [c for c in first if c.get("cache_indices") == "visits"]
         assert visits and all(c["block_threads"] == bt for c in visits)
@@ -60,13 +60,15 @@ def test_candidate_rounds():
         for c in first:
             r = autotune.refinements(c, 439)
             if "specialize" in c:
-                assert r == [dict(c, specialize=64)]
+                assert r == [dict(c, specialize=32), dict(c, specialize=64)]
             else:
                 assert r == []
-    # few classes: one count only, no second round
+    # few classes: the counts stop at the class count
     few = autotune.candidate_list(True, 20, 4, optin)
-    assert {c["specialize"] for c in few if "specialize" in c} == {20}
-    assert all(autotune.refinements(c, 20) == [] for c in few)
+    assert {c["specialize"] for c in few if "specialize" in c} == {16}
+    assert all(autotune.refinements(c, 20) == ([dict(c, specialize=20)] if "specialize" in c else [])
+               for c in few)
+    assert autotune.refinements(dict(specialize=16), 12) == []
     assert autotune.refinements(dict(specialize=32), 40) == [dict(specialize=40)]
     # outside the class programs: general kernels and the atomic scheme only
     gen = autotune.candidate_list(False, 0, 8, optin)
