@@ -212,6 +212,10 @@ def make_config(mode=MODE_OWNER, chunk_entries=0, block_threads=0, group_lanes=0
                 debug_checks=False, force_spill=False, class_programs=True,
                 visit_block_log2=0, specialize=False, cache_indices=False, general_kernel=0,
                 compact_chunks=False, specialize_in_batch=False, specialize_async=False) -> _Config:
+    """A ptap_config (fields as in include/ptap.h).  specialize: True for 8 classes or a count;
+    cache_indices: False, True (P row starts per entry of A) or "visits" (piece records: the
+    indices cached per visit of a fine row to a chunk); specialize_in_batch: leave the compile
+    to a Batch over this plan; specialize_async: compile in a background thread."""
     cfg = _Config()
     cfg.mode = mode
     cfg.chunk_entries = chunk_entries
