@@ -54,7 +54,8 @@ def candidate_list(fast_path: bool, n_classes: int, value_bytes: int, smem_optin
     """First-round candidate configurations (ptap.make_config keywords) for one problem.
 
     fast_path / n_classes come from a default symbolic pass.  For class-program
-    plans: CTAs of 512 and 1024 threads, each with the largest chunk the
+    plans: CTAs of the size the compiled code keeps resident (1024 threads for
+    4-byte values, 512 for 8-byte ones), with the largest chunk the
     accumulator allows and smaller ones (fewer entries per CTA: more CTAs for
     the same C, more fine rows visiting two chunks), without cached indices,
     with the cached P row start per entry of A, and with the indices cached
@@ -72,22 +73,22 @@ def candidate_list(fast_path: bool, n_classes: int, value_bytes: int, smem_optin
         lim = chunk_limit(value_bytes, smem_optin)
         k = _spec_counts(n_classes)[0]
         mid = 32768 if lim > 32768 else max(1024, (lim * 5 // 6) & ~4095)
-        for bt in (1024, 512):
-            chunks = sorted({lim, mid, max(1024, lim // 2)}, reverse=True)
-            for ch in chunks:
-                out.append(dict(specialize=k, block_threads=bt, chunk_entries=ch))
-            # the plan's cached indices (Section 4.2's memory-for-time trade), every chunk size:
-            # per entry of A, and per visit
-            for ch in chunks:
-                out.append(dict(specialize=k, block_threads=bt, chunk_entries=ch, cache_indices=True))
-            # per visit: only with the CTA size the compiled code is built to keep resident
-            # (1024 threads for 4-byte values, 512 for 8-byte ones, whose code holds twice
-            # the registers)
-            if bt == (1024 if value_bytes <= 4 else 512):
-                rec_chunks = sorted(set(chunks) | ({(mid + lim) // 2 & ~4095} if lim > mid + 4096 else set()),
-                                    reverse=True)
-                for ch in rec_chunks:
-                    out.append(dict(specialize=k, block_threads=bt, chunk_entries=ch, cache_indices="visits"))
+        # compiled classes: the CTA size their code is built to keep resident, one CTA per SM
+        # (1024 threads for 4-byte values; 512 for 8-byte ones, whose code holds twice the
+        # registers).  The other size measured 1.5-3x slower on every problem tried, from
+        # spills or half the threads per SM.
+        bt = 1024 if value_bytes <= 4 else 512
+        chunks = sorted({lim, mid, max(1024, lim // 2)}, reverse=True)
+        for ch in chunks:
+            out.append(dict(specialize=k, block_threads=bt, chunk_entries=ch))
+        # the plan's cached indices (Section 4.2's memory-for-time trade), every chunk size:
+        # per entry of A, and per visit
+        for ch in chunks:
+            out.append(dict(specialize=k, block_threads=bt, chunk_entries=ch, cache_indices=True))
+        rec_chunks = sorted(set(chunks) | ({(mid + lim) // 2 & ~4095} if lim > mid + 4096 else set()),
+                            reverse=True)
+        for ch in rec_chunks:
+            out.append(dict(specialize=k, block_threads=bt, chunk_entries=ch, cache_indices="visits"))
         out.append(dict())                                    # interpreter, 256 threads
         out.append(dict(block_threads=1024, chunk_entries=lim))  # interpreter, large CTAs
     out.append(dict(class_programs=False))                   # sort-based general kernel
